@@ -1,0 +1,172 @@
+"""Seeded synthetic inputs for the distilled-nucleon hot path.
+
+This module holds no arithmetic of the method itself.  It only draws the
+random inputs that the elementals and the correlation matrix consume, in the
+shapes of the workloads of the nucleon study (distillation with N_v
+Laplacian-eigenvector fields per timeslice, perambulators between spin-mode
+indices, quark distillation profiles, lattice momenta; Sec. 2.1 of the
+paper).  Both the FP64 oracle and the CUDA path read inputs drawn here, so
+both see identical bytes.
+
+Conventions (all fixed here, used by every consumer):
+
+* site order  s = x + L*(y + L*z),  x, y, z in 0..L-1;  V3 = L**3.
+* eigenvector fields  v[t][i][s][a]  (mode i, site s, colour a fastest);
+  the N_v columns of the (3*V3) x N_v matrix with rows (s, a) are an
+  orthonormal set (seeded complex Gaussian, orthonormalised by Cholesky-QR).
+* perambulators  tau[t][I][I'],  I = alpha*N_v + i  (spin-major), complex
+  Gaussian blocks with unit complex variance, scaled by exp(-decay*t).
+* profiles  prof[b][i]  real, index form g_i = exp(-(i/N_v)^2 / sigma^2) or
+  the index-linear g_i = 1 - i/N_v.
+* momenta  mom[q] = integer triples n, p = 2*pi*n/L.
+
+Random streams: numpy PCG64 seeded by SeedSequence(2609, spawn_key=(config,
+cfg, t, field)) with field 0 = eigenvectors, 1 = perambulator, 2 = N_v draw.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+BASE_SEED = 2609
+FIELD_V, FIELD_TAU, FIELD_NV = 0, 1, 2
+
+
+def rng_for(config: int, cfg: int, t: int, field: int) -> np.random.Generator:
+    ss = np.random.SeedSequence(BASE_SEED, spawn_key=(config, cfg, t, field))
+    return np.random.Generator(np.random.PCG64(ss))
+
+
+def complex_gaussian(rng: np.random.Generator, shape) -> np.ndarray:
+    """Re, Im ~ N(0, 1/2) independently: unit complex variance."""
+    re = rng.standard_normal(shape)
+    im = rng.standard_normal(shape)
+    return (re + 1j * im) * math.sqrt(0.5)
+
+
+def orthonormal_columns(a: np.ndarray) -> np.ndarray:
+    """Orthonormalise the columns of a tall complex matrix (Cholesky-QR, twice).
+
+    Q = A R^{-1} with R^H R = A^H A.  A second pass removes the O(u*cond^2)
+    loss of orthogonality; for Gaussian A the result is orthonormal to
+    rounding.  Any unitary mixing of the columns would do: the consumers read
+    the bytes produced here.
+    """
+    q = a
+    for _ in range(2):
+        g = q.conj().T @ q
+        r = np.linalg.cholesky(g).conj().T  # upper triangular, g = r^H r
+        q = solve_triangular(r, q.T, trans="T", lower=False).T  # q r^{-1}
+    return q
+
+
+@dataclasses.dataclass
+class Problem:
+    """One distillation workload (one gauge configuration)."""
+    name: str
+    L: int
+    nt: int
+    nv: int
+    mom: np.ndarray          # [np][3] int32
+    prof: np.ndarray         # [nb][nv] float64 (t-independent profiles)
+    tau_decay: float
+    dtype: np.dtype          # complex128 or complex64 storage of v and tau
+    config_id: int = 0
+    cfg: int = 0
+
+    @property
+    def V3(self) -> int:
+        return self.L ** 3
+
+    @property
+    def np_(self) -> int:
+        return int(self.mom.shape[0])
+
+    @property
+    def nb(self) -> int:
+        return int(self.prof.shape[0])
+
+    @property
+    def T3(self) -> int:
+        return self.nv * (self.nv - 1) * (self.nv - 2) // 6
+
+    def eigvecs(self, t: int) -> np.ndarray:
+        """v[t]: [nv][V3][3] orthonormal over the (site, colour) index."""
+        rng = rng_for(self.config_id, self.cfg, t, FIELD_V)
+        a = complex_gaussian(rng, (3 * self.V3, self.nv))
+        q = orthonormal_columns(a)
+        return np.ascontiguousarray(q.T.reshape(self.nv, self.V3, 3)).astype(self.dtype)
+
+    def perambulator(self, t: int) -> np.ndarray:
+        """tau[t]: [4nv][4nv] complex Gaussian times exp(-decay*t)."""
+        rng = rng_for(self.config_id, self.cfg, t, FIELD_TAU)
+        n4 = 4 * self.nv
+        return (complex_gaussian(rng, (n4, n4)) * math.exp(-self.tau_decay * t)).astype(self.dtype)
+
+    def all_eigvecs(self, ts: Optional[Sequence[int]] = None) -> np.ndarray:
+        ts = range(self.nt) if ts is None else ts
+        return np.stack([self.eigvecs(t) for t in ts])
+
+    def all_perambulators(self, ts: Optional[Sequence[int]] = None) -> np.ndarray:
+        ts = range(self.nt) if ts is None else ts
+        return np.stack([self.perambulator(t) for t in ts])
+
+
+def gaussian_profiles(nv: int, sigmas: Sequence[float]) -> np.ndarray:
+    i = np.arange(nv, dtype=np.float64)
+    return np.stack([np.exp(-((i / nv) ** 2) / (s * s)) for s in sigmas])
+
+
+def linear_profile(nv: int) -> np.ndarray:
+    return 1.0 - np.arange(nv, dtype=np.float64) / nv
+
+
+MOM_C1 = [(0, 0, 0), (1, 0, 0)]
+MOM_C2 = [(0, 0, 0), (1, 0, 0), (1, 1, 0)]
+MOM_C3 = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, 1)]
+MOM_C4 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+MOM_C5 = MOM_C4 + [(1, 1, 0), (1, 1, 1)]
+
+
+def _mom(lst) -> np.ndarray:
+    return np.asarray(lst, dtype=np.int32).reshape(-1, 3)
+
+
+def config(cid: int, cfg: int = 0) -> Problem:
+    """The five workloads: 1 small FP64, 2 medium, 3 mixed-precision,
+    4 batched uneven-N_v ensemble (one member), 5 large."""
+    if cid == 1:
+        return Problem("L8_Nt8_Nv16", 8, 8, 16, _mom(MOM_C1),
+                       gaussian_profiles(16, [0.3, 0.6, 1.0]), 0.5, np.complex128, 1, cfg)
+    if cid == 2:
+        prof = np.concatenate([gaussian_profiles(64, [0.3, 0.6, 1.0]), linear_profile(64)[None]])
+        return Problem("L24_Nt48_Nv64", 24, 48, 64, _mom(MOM_C2), prof, 0.4, np.complex64, 2, cfg)
+    if cid == 3:
+        sig = [0.2 * 6.0 ** (a / 5.0) for a in range(6)]
+        return Problem("L32_Nt64_Nv128", 32, 64, 128, _mom(MOM_C3),
+                       gaussian_profiles(128, sig), 0.4, np.complex64, 3, cfg)
+    if cid == 4:
+        nv = int(rng_for(4, cfg, 0, FIELD_NV).choice([64, 96, 128]))
+        sig = [0.2 * 6.0 ** (a / 5.0) for a in range(6)]
+        return Problem(f"L32_Nt64_cfg{cfg}_Nv{nv}", 32, 64, nv, _mom(MOM_C4),
+                       gaussian_profiles(nv, sig), 0.4, np.complex64, 4, cfg)
+    if cid == 5:
+        sig = [0.2 * 6.0 ** (a / 7.0) for a in range(8)]
+        return Problem("L48_Nt96_Nv256", 48, 96, 256, _mom(MOM_C5),
+                       gaussian_profiles(256, sig), 0.4, np.complex64, 5, cfg)
+    raise ValueError(f"unknown workload {cid}")
+
+
+def ensemble4(ncfg: int = 16) -> List[Problem]:
+    return [config(4, c) for c in range(ncfg)]
+
+
+def small(L: int, nt: int, nv: int, mom=MOM_C1, sigmas=(0.3, 0.6, 1.0), decay=0.5,
+          dtype=np.complex128, seed_cfg: int = 0) -> Problem:
+    """Small problems for tests (config id 0, cfg = seed_cfg)."""
+    return Problem(f"L{L}_Nt{nt}_Nv{nv}", L, nt, nv, _mom(mom),
+                   gaussian_profiles(nv, sigmas), decay, np.dtype(dtype), 0, seed_cfg)
