@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Throughput of the distilled-nucleon hot path on B300.
+
+One step = the whole hot path for one gauge configuration of the workload:
+elementals Phi[t][p] for every timeslice and momentum, the N_B x N_B
+correlation matrix C_ab(t) for every (t, p) (source at t0 = 0) and the GEVP
+of every (p, t).  The metric is C_ab(t) entries per second (N_p N_B^2 N_t
+entries per step per configuration); algorithmic TFLOP/s is reported beside
+it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 3]
+                    [--mode fp16x3|bf16x6|bf16x3|fp32|fp64] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank processes its own
+configuration (cfg = rank): weak scaling, no collective on the data path;
+the step time is the max over ranks.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_37723_b300 import synth  # noqa: E402  (host-only, no CUDA)
+
+METRIC = "C_ab(t) entries/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+# --------------------------------------------------------------------------- inputs
+
+def _eig_worker(args):
+    cid, cfg, t = args
+    return synth.config(cid, cfg).eigvecs(t)
+
+
+def make_inputs(cid: int, cfg: int, workers: int):
+    """Host inputs of one configuration (numpy, identical bytes to the tests)."""
+    p = synth.config(cid, cfg)
+    if workers > 1 and p.nt > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            vs = pool.map(_eig_worker, [(cid, cfg, t) for t in range(p.nt)])
+        v = np.stack(vs)
+    else:
+        v = p.all_eigvecs()
+    tau = p.all_perambulators()
+    return p, v, tau
+
+
+# --------------------------------------------------------------------------- flops
+
+def algorithmic_flops(p: synth.Problem) -> dict:
+    """Counting convention for TFLOP/s (8 real flops per complex MAC):
+    elementals 8*3V3*T3 per (t, p) (i<j<k only) and correlator
+    8*92*N_B*N_v^4 per (t, p)."""
+    tp = p.nt * p.np_
+    el = 8.0 * 3 * p.V3 * p.T3 * tp
+    co = 8.0 * 92 * p.nb * p.nv ** 4 * tp
+    return {"elementals": el, "correlator": co, "total": el + co}
+
+
+def executed_cmacs(p: synth.Problem) -> dict:
+    """Complex MACs the library's contraction kernels execute per step:
+    elementals np*nv x P2 x 3V3 dense tiles (triangle-skipped at tile level,
+    counted dense here), correlator 12 N_B n^4 (step i) + 24 N_B n^4 (step j)
+    + 2.5 N_B n^4 (source, i'<j') per (t, p)."""
+    n = p.nv
+    P2 = n * (n - 1) // 2
+    tp = p.nt * p.np_
+    return {"step_i": 12.0 * p.nb * n ** 4 * tp, "step_j": 24.0 * p.nb * n ** 4 * tp,
+            "source": 5.0 * p.nb * P2 * n * n * tp}
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- cpu baseline
+
+def cpu_baseline(cid: int, budget_s: float = 15.0) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    timeslices t = 1, 2, ... at momentum index 0 (elementals of that t and
+    momentum, then that C_ab(t)), plus the source elementals at t = 0,
+    until about `budget_s` seconds of CPU work are spent."""
+    from oracle import nucleon as orc
+    p = synth.config(cid, 0)
+    mom0 = p.mom[:1]
+    t0 = time.perf_counter()
+    v0 = p.eigvecs(0)
+    gen = time.perf_counter() - t0
+    t_start = time.perf_counter()
+    phi_src = orc.elementals_t(v0, p.L, mom0)[0]
+    done = 0
+    t = 1
+    gen_total = gen
+    while t < p.nt:
+        g0 = time.perf_counter()
+        vt = p.eigvecs(t)
+        tau = p.perambulator(t)
+        gen_total += time.perf_counter() - g0
+        phi = orc.elementals_t(vt, p.L, mom0)[0]
+        orc.correlator_tp(phi, phi_src, tau, p.prof, p.prof)
+        done += 1
+        t += 1
+        if time.perf_counter() - t_start - (gen_total - gen) > budget_s:
+            break
+    elapsed = time.perf_counter() - t_start - (gen_total - gen)
+    entries = done * p.nb * p.nb
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) if \
+            threadpoolctl.threadpool_info() else 1
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": entries / elapsed, "unit": METRIC, "cores": int(cores), "kind": "oracle",
+            "sample": f"{done} (t, p=0) slices t=1..{done} of {p.nt * p.np_}, plus source elementals "
+                      f"at t=0; {elapsed:.1f} s; numpy FP64 with BLAS threads",
+            "seconds": elapsed}
+
+
+# --------------------------------------------------------------------------- ours
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cid = args.workload
+    workers = min(16, os.cpu_count() or 1)
+    p, v_h, tau_h = make_inputs(cid, rank, workers)   # before any CUDA call
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2609_37723_b300 import distil
+    mode = args.mode
+    if mode == "auto":
+        mode = next((m for m in ("fp16x3", "bf16x6") if distil.mode_available(m)), "fp32")
+    c128 = mode == "fp64"
+    cdt = np.complex128 if c128 else np.complex64
+    v_h = np.ascontiguousarray(v_h.astype(cdt))
+    tau_h = np.ascontiguousarray(tau_h.astype(cdt))
+    prof_h = np.ascontiguousarray(p.prof)
+    t0_gevp = min(2, p.nt - 1)
+
+    # pinned host copies for the end-to-end leg
+    v_pin = torch.from_numpy(v_h).pin_memory()
+    tau_pin = torch.from_numpy(tau_h).pin_memory()
+    prof_pin = torch.from_numpy(prof_h).pin_memory()
+    v = v_pin.to(dev)
+    tau = tau_pin.to(dev)
+    prof = prof_pin.to(dev)
+    stream = torch.cuda.current_stream()
+
+    T3 = p.T3
+    tdt = torch.complex128 if c128 else torch.complex64
+    phi = torch.empty((p.nt, p.np_, T3), dtype=tdt, device=dev)
+    C = torch.empty((p.np_, p.nb, p.nb, p.nt), dtype=torch.complex128, device=dev)
+    lam = torch.empty((p.np_, p.nt, p.nb), dtype=torch.complex128, device=dev)
+    ws_e = distil.elementals_workspace(p.L, p.nt, p.nv, p.np_, mode)
+    ws_c = distil.correlate_workspace(p.nt, p.nv, p.np_, p.nb, mode)
+    ws = torch.empty(max(ws_e, ws_c, 1), dtype=torch.uint8, device=dev)
+
+    def step(vv, tt, pp):
+        distil.elementals(vv, p.L, p.mom, mode, out=phi, workspace=ws)
+        distil.correlate(phi, phi[0], tt, pp, mode, out=C, workspace=ws)
+        distil.gevp(C, t0_gevp, out=lam)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(v, tau, prof)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (device-resident inputs)
+    distil.profile_enable(timing=True, device=local)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(v, tau, prof)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kstats = distil.profile_read(device=local)
+    distil.profile_enable(timing=False, device=local)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    entries = p.np_ * p.nb * p.nb * p.nt
+    value = world * entries * args.steps / (ms / 1e3)
+
+    # ---------------- end to end through the public API (host in, host out)
+    C_host = torch.empty(C.shape, dtype=C.dtype).pin_memory()
+    lam_host = torch.empty(lam.shape, dtype=lam.dtype).pin_memory()
+    vin = torch.empty_like(v)
+    tin = torch.empty_like(tau)
+    pin_ = torch.empty_like(prof)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        vin.copy_(v_pin, non_blocking=True)
+        tin.copy_(tau_pin, non_blocking=True)
+        pin_.copy_(prof_pin, non_blocking=True)
+        step(vin, tin, pin_)
+        C_host.copy_(C, non_blocking=True)
+        lam_host.copy_(lam, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = v_h.nbytes + tau_h.nbytes + prof_h.nbytes
+    d2h = C_host.numel() * 16 + lam_host.numel() * 16
+
+    # ---------------- parity of this run against the oracle on one slice (rank 0)
+    out = None
+    if rank == 0:
+        flops = algorithmic_flops(p)
+        pk = peaks()
+        gemm_names = [k for k in kstats if k.startswith(("tc_gemm", "simt_gemm", "elementals"))]
+        dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+        roof = roofline(dom, kstats, p, mode, pk, args.steps)
+        launches = sum(l for l, _ in kstats.values())
+        parity = parity_slice(p, v_h, tau_h, C.cpu().numpy(), mode) if not args.no_parity else None
+        cpu = None if args.no_cpu_baseline else cpu_baseline(cid, args.cpu_budget)
+        out = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(mode, mode + "(f32 accumulate)"),
+            "data": "synthetic (seeded orthonormal eigenvectors, Gaussian perambulators)",
+            "config": {"workload": p.name, "L": p.L, "nt": p.nt, "nv": p.nv, "np": p.np_, "nb": p.nb,
+                       "mode": mode, "cfg_per_rank": 1, "parallelism": f"weak x{world} (cfg = rank)",
+                       "l2": "inputs larger than L2 (v is %.1f GB)" % (v_h.nbytes / 1e9)},
+            "tflops_algorithmic": flops["total"] * world / (ms_step / 1e3) / 1e12,
+            "e2e": {"value": world * entries * e2e_steps / (ms_e2e / 1e3), "unit": "entries/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in sorted(kstats.items(),
+                                                                                  key=lambda kv: -kv[1][1])},
+            "roofline": roof,
+            "clocks": clk,
+            "parity": parity,
+            "cpu_baseline": cpu,
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def roofline(dom, kstats, p, mode, pk, steps):
+    """Roofline of the dominant kernel family over the timed region."""
+    if dom is None:
+        return None
+    launches, ms = kstats[dom]
+    n = p.nv
+    tp = p.nt * p.np_
+    P2 = n * (n - 1) // 2
+    if dom.startswith("elementals"):
+        cm = 3.0 * p.V3 * p.T3 * tp          # useful complex MACs (i<j<k)
+        what = "elementals: 3 V3 T3 complex MACs per (t,p)"
+    elif "gemm" in dom:
+        cm = (12 + 24) * p.nb * n ** 4 * tp + 5.0 * p.nb * P2 * n * n * tp
+        what = "mode contractions: (36 N_B n^4 + 2.5 N_B n^4) complex MACs per (t,p)"
+    else:
+        return {"kernel": dom, "note": "no flop model"}
+    flop = 8.0 * cm * steps
+    achieved = flop / (ms / 1e3) / 1e12
+    if mode in ("fp64", "fp32"):
+        peak = None
+        bound = "alu"
+        note = "CUDA-core path; peak FP32/FP64 SIMT not in MEASURED_PEAKS"
+    else:
+        prod = {"bf16x6": 6, "bf16x3": 3, "fp16x3": 3}[mode]
+        peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
+        achieved *= prod   # issued 16-bit tensor flops
+        bound = "tensor"
+        note = f"issued {prod} split products per complex MAC vs measured bf16 sustained peak"
+    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if peak else None, "traffic": None, "per_unit": what,
+            "launches": launches, "ms": ms, "note": note}
+
+
+def parity_slice(p, v_h, tau_h, C_gpu, mode):
+    """FP64 oracle on (t=1, p=0) of this run's inputs vs the benchmarked C."""
+    try:
+        from oracle import nucleon as orc
+        t = 1 if p.nt > 1 else 0
+        mom0 = p.mom[:1]
+        phi0 = orc.elementals_t(v_h[0], p.L, mom0)[0]
+        phit = orc.elementals_t(v_h[t], p.L, mom0)[0]
+        ref = orc.correlator_tp(phit, phi0, tau_h[t], p.prof, p.prof)
+        got = C_gpu[0, :, :, t]
+        err = np.abs(got - ref) / np.abs(ref)
+        return {"slice": f"t={t}, p=0", "max_rel_err": float(err.max()),
+                "normwise": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    except Exception as e:  # report, never hide
+        return {"error": repr(e)}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    p = synth.config(args.workload, 0)
+    cb = cpu_baseline(args.workload, args.cpu_budget)
+    steps_ms = []
+    for _ in range(args.warmup + args.steps):
+        pass
+    val = cb["value"]
+    return {"metric": METRIC, "value": val, "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": p.np_ * p.nb * p.nb * p.nt / val * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": p.name, "L": p.L, "nt": p.nt, "nv": p.nv, "np": p.np_, "nb": p.nb},
+            "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--mode", default="auto")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

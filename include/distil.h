@@ -1,0 +1,172 @@
+/*
+ * distil.h -- C interface of the B300 distilled-nucleon library.
+ *
+ * Computes, on one GPU, the hot path of the nucleon operators with quark
+ * distillation profiles (paper: "Improving hadron creation operators for
+ * charmonium, glueballs and baryons", Sec. 2.1 "Improved nucleon
+ * operators"):
+ *
+ *   elementals   Phi[p,t]_ijk = sum_x exp(-i p.x) eps_abc v_i^a v_j^b v_k^c
+ *                (the nucleon elementals / "triplets" the paper rescales;
+ *                the paper names them but prints no formula, this is the
+ *                standard baryon elemental without displacement or 1/V3),
+ *   correlate    the N_B x N_B matrix C_ab(t) of the profiled elementals
+ *                Phi^(a) = g^(a)_i g^(a)_j g^(a)_k Phi_ijk (Sec. 2.1,
+ *                displayed equation, no sums) between a sink at t and a
+ *                source at t0 = 0 through perambulators tau(t, t0), with the
+ *                positive-parity C gamma_5 nucleon spin structure and the
+ *                direct minus exchange u-quark Wick terms,
+ *   gevp         the generalized eigenvalues of C(t) u = lambda C(t0) u
+ *                (Sec. 2.1, "solve a GEVP").
+ *
+ * Conventions common to every call
+ * --------------------------------
+ *  - Complex numbers are interleaved (re, im) pairs: "c128" = two doubles,
+ *    "c64" = two floats.  Arrays are row-major, last index fastest.
+ *  - All array pointers are DEVICE pointers on the context's device, owned
+ *    by the caller; the library never frees them.  Exceptions are named
+ *    (the momentum list is a host pointer).
+ *  - Calls are asynchronous on the given CUDA stream (0 = legacy default
+ *    stream) unless stated.  Workspace passed to a call must stay untouched
+ *    until the stream has passed the call.
+ *  - Every call returns a distil_status.  On error nothing has been
+ *    enqueued (argument errors) or the stream may hold partial results
+ *    (DISTIL_ECUDA, DISTIL_ETIMEOUT); distil_last_error() gives a message.
+ *    No call traps or aborts the device on bad input.
+ *  - Site order s = x + L*(y + L*z).  Momentum p = 2*pi*n/L for integer n.
+ *  - Packed triples: i<j<k stored at colex rank C(k,3) + C(j,2) + i,
+ *    T3 = nv*(nv-1)*(nv-2)/6 entries.
+ *  - Spin-mode index of a perambulator: I = alpha*nv + i (alpha in 0..3),
+ *    Dirac-Pauli basis with gamma_4 = diag(1,1,-1,-1).
+ */
+#ifndef DISTIL_H
+#define DISTIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* distil_stream; /* same type as cudaStream_t */
+
+typedef enum {
+  DISTIL_OK = 0,
+  DISTIL_EINVAL = 1,   /* bad argument (null pointer, size, mode)          */
+  DISTIL_ENOMEM = 2,   /* workspace too small / allocation failed          */
+  DISTIL_ECUDA = 3,    /* a CUDA runtime or driver call failed             */
+  DISTIL_ETIMEOUT = 4, /* a bounded device-side wait expired               */
+  DISTIL_ENOTSUP = 5   /* mode or size not supported by this build         */
+} distil_status;
+
+/* Arithmetic of a call.  Storage types follow the mode: FP64 reads and
+ * writes c128; every other mode reads c64 eigenvectors / perambulators /
+ * elementals.  The correlation matrix and GEVP are always c128. */
+typedef enum {
+  DISTIL_FP64 = 0,        /* plain FP64 on CUDA cores                        */
+  DISTIL_FP32 = 1,        /* plain FP32 on CUDA cores, FP64 final sums       */
+  DISTIL_MIXED_BF16X6 = 2,/* tensor cores: 3-piece BF16 split, 6 products    */
+  DISTIL_MIXED_BF16X3 = 3,/* tensor cores: 2-piece BF16 split, 3 products    */
+  DISTIL_MIXED_FP16X3 = 4 /* tensor cores: 2-piece FP16 split, 3 products,
+                             power-of-two operand scaling                    */
+} distil_mode;
+
+typedef struct distil_ctx distil_ctx;
+
+/* Create a context on CUDA device `device` (makes it current for the
+ * calling thread).  *out receives the handle.  One context per device. */
+int distil_create(int device, distil_ctx** out);
+
+/* Release the context and the small device buffers it owns (error word,
+ * phase tables).  Waits for nothing: synchronise the streams first. */
+void distil_destroy(distil_ctx* ctx);
+
+/* Message of the last failed call made by this thread ("" if none).  The
+ * string is owned by the library and valid until the next call. */
+const char* distil_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Elementals                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of device workspace distil_elementals needs for these sizes. */
+int distil_elementals_workspace(int L, int nt, int nv, int np, int mode, size_t* bytes);
+
+/* Phi[t][q][r] = sum_s exp(-i p_q.x_s) det[v_i(s), v_j(s), v_k(s)] for the
+ * triple of rank r, for t < nt and q < np.
+ *   v    [nt][nv][L^3][3]   c128 (FP64) or c64 (other modes), device
+ *   mom  [np][3] int32      integer momenta n, HOST pointer, read during the call
+ *   phi  [nt][np][T3]       c128 (FP64) or c64, device, fully overwritten
+ * Sizes: 1 <= L <= 256, nt >= 1, nv >= 1 (nv < 3 gives T3 = 0), np >= 1.
+ * The elementals are the paper's Phi[p,t]_ijk before profiles (Sec. 2.1). */
+int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv,
+                      const int32_t* mom, int np, int mode, void* phi,
+                      void* workspace, size_t ws_bytes, distil_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Correlation matrix                                                  */
+/* ------------------------------------------------------------------ */
+
+int distil_correlate_workspace(int nt, int nv, int np, int nb, int mode, size_t* bytes);
+
+/* C[q][a][b][t] = sum_{mu nu} P+_{nu mu} sum Psi^(a)mu_{IJK}(t) tau_II' tau_JJ' tau_KK'
+ *                 [Psi^(b)nu_{I'J'K'}(0) - Psi^(b)nu_{K'J'I'}(0)]^*
+ * with Psi^(a)mu_{(alpha i)(beta j)(gamma k)} = g^(a)_i g^(a)_j g^(a)_k
+ * Phi_ijk (C gamma_5)_{alpha beta} delta_{gamma mu}.
+ *   phi_snk [nt][np][T3]      sink elementals at t (c128 FP64, else c64)
+ *   phi_src [np][T3]          source elementals at t0 = 0 (same type)
+ *   tau     [nt][4nv][4nv]    tau(t, t0) spin-major (same type)
+ *   prof    [nb][nv] f64, or [nt][nb][nv] when prof_per_t != 0 (sink uses
+ *           g[t], source g[0]); device pointer
+ *   C       [np][nb][nb][nt]  c128, device, fully overwritten
+ * Sizes: nv >= 1, nt >= 1, np >= 1, 1 <= nb <= 16. */
+int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src,
+                     const void* tau, int nt, int nv, int np,
+                     const double* prof, int nb, int prof_per_t, int mode,
+                     void* C, void* workspace, size_t ws_bytes, distil_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* GEVP                                                                */
+/* ------------------------------------------------------------------ */
+
+/* lambda[q][t][n] = generalized eigenvalues of C[q][:][:][t] u = lambda
+ * C[q][:][:][t0] u, FP64, sorted by |lambda| descending.  General
+ * (non-Hermitian) pencils: C(t0)^{-1} C(t) by LU with partial pivoting,
+ * then Hessenberg reduction and shifted complex QR.  A singular C(t0) or
+ * a QR sweep that fails to converge gives NaN eigenvalues for that (q, t)
+ * and the call still returns DISTIL_OK.
+ *   C       [np][nb][nb][nt] c128 device;  lambda [np][nt][nb] c128 device.
+ * Sizes: 1 <= nb <= 16, 0 <= t0 < nt. */
+int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0,
+                void* lambda, distil_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Introspection                                                       */
+/* ------------------------------------------------------------------ */
+
+/* 1 if this build implements `mode`, else 0 (no device needed). */
+int distil_mode_supported(int mode);
+
+/* Per-kernel statistics of the library's own launches. */
+typedef struct {
+  char name[64];       /* kernel family, e.g. "simt_gemm_f64"            */
+  long long launches;  /* launches since the last distil_profile_enable  */
+  double ms;           /* summed event-timed duration (0 if not timing)  */
+} distil_kernel_stat;
+
+/* Reset the per-kernel counters of ctx (synchronises the device first).
+ * timing != 0 additionally brackets every later launch with a pair of CUDA
+ * events recorded on the launching stream.  Launch counting is always on.
+ * Do not enable timing while a stream of ctx is being captured into a
+ * CUDA graph. */
+int distil_profile_enable(distil_ctx* ctx, int timing);
+
+/* Copy up to `max` kernel statistics into out[] and the number of kernel
+ * families seen into *count.  Waits for the recorded events to complete. */
+int distil_profile_read(distil_ctx* ctx, distil_kernel_stat* out, int max, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DISTIL_H */

@@ -1,0 +1,196 @@
+// C-ABI entry points of libdistil (declared in include/distil.h): argument
+// validation, workspace accounting and dispatch to the kernels of each mode.
+#include <stdarg.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "correlate.cuh"
+#include "elementals.cuh"
+#include "mixed.cuh"
+#include "prof.cuh"
+
+namespace distil {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* get_error() { return g_err; }
+
+int gevp_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, void* lambda, cudaStream_t s);
+
+Profiler& profiler(distil_ctx* ctx) { return *ctx->prof; }
+
+// Make the context's device current for this call.
+static int enter(distil_ctx* ctx) {
+  if (!ctx) {
+    set_error("null context");
+    return DISTIL_EINVAL;
+  }
+  DISTIL_CUDA(cudaSetDevice(ctx->device));
+  return DISTIL_OK;
+}
+
+}  // namespace distil
+
+using namespace distil;
+
+extern "C" {
+
+int distil_create(int device, distil_ctx** out) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(out != nullptr, "distil_create: out is null");
+  *out = nullptr;
+  int ndev = 0;
+  DISTIL_CUDA(cudaGetDeviceCount(&ndev));
+  DISTIL_CHECK_ARG(device >= 0 && device < ndev, "distil_create: device %d not in [0,%d)", device, ndev);
+  DISTIL_CUDA(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  DISTIL_CUDA(cudaGetDeviceProperties(&prop, device));
+  distil_ctx* c = new distil_ctx();
+  c->device = device;
+  c->sm_count = prop.multiProcessorCount;
+  c->cc_major = prop.major;
+  c->cc_minor = prop.minor;
+  c->d_error = nullptr;
+  c->prof = new Profiler();
+  if (cudaMalloc(&c->d_error, sizeof(unsigned int) * 4) != cudaSuccess ||
+      cudaMemset(c->d_error, 0, sizeof(unsigned int) * 4) != cudaSuccess) {
+    set_error("distil_create: cannot allocate the device error word");
+    delete c->prof;
+    delete c;
+    return DISTIL_ENOMEM;
+  }
+  *out = c;
+  return DISTIL_OK;
+}
+
+void distil_destroy(distil_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->d_error) cudaFree(ctx->d_error);
+  delete ctx->prof;
+  delete ctx;
+}
+
+const char* distil_last_error(void) { return get_error(); }
+
+int distil_elementals_workspace(int L, int nt, int nv, int np, int mode, size_t* bytes) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
+  DISTIL_CHECK_ARG(valid_mode(mode), "bad mode %d", mode);
+  DISTIL_CHECK_ARG(L >= 1 && nt >= 1 && nv >= 1 && np >= 1, "bad sizes");
+  *bytes = is_mixed(mode) ? elementals_mixed_workspace(L, nt, nv, np, mode) : 0;
+  return DISTIL_OK;
+}
+
+int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv, const int32_t* mom, int np,
+                      int mode, void* phi, void* workspace, size_t ws_bytes, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(valid_mode(mode), "distil_elementals: bad mode %d", mode);
+  DISTIL_CHECK_ARG(L >= 1 && L <= EL_MAX_L, "distil_elementals: L=%d outside [1,%d]", L, EL_MAX_L);
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1, "distil_elementals: nt, nv, np must be >= 1");
+  DISTIL_CHECK_ARG(np <= EL_MAX_MOM, "distil_elementals: at most %d momenta per call", EL_MAX_MOM);
+  DISTIL_CHECK_ARG(v && mom && phi, "distil_elementals: null pointer");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (mode == DISTIL_FP64)
+    return elementals_simt<double>(ctx, (const Cx<double>*)v, L, nt, nv, mom, np, (Cx<double>*)phi, s);
+  if (mode == DISTIL_FP32)
+    return elementals_simt<float>(ctx, (const Cx<float>*)v, L, nt, nv, mom, np, (Cx<float>*)phi, s);
+  size_t need = elementals_mixed_workspace(L, nt, nv, np, mode);
+  if (ws_bytes < need || (need && !workspace)) {
+    set_error("distil_elementals: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  return elementals_mixed(ctx, (const Cx<float>*)v, L, nt, nv, mom, np, mode, (Cx<float>*)phi, workspace,
+                          ws_bytes, s);
+}
+
+int distil_correlate_workspace(int nt, int nv, int np, int nb, int mode, size_t* bytes) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
+  DISTIL_CHECK_ARG(valid_mode(mode), "bad mode %d", mode);
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1 && nb >= 1 && nb <= 16, "bad sizes");
+  if (is_mixed(mode)) *bytes = correlate_mixed_workspace(mode, nv, nb);
+  else *bytes = correlate_plain_workspace(mode == DISTIL_FP64, nv, nb);
+  return DISTIL_OK;
+}
+
+int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, const void* tau, int nt, int nv,
+                     int np, const double* prof, int nb, int prof_per_t, int mode, void* C, void* workspace,
+                     size_t ws_bytes, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(valid_mode(mode), "distil_correlate: bad mode %d", mode);
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1, "distil_correlate: nt, nv, np must be >= 1");
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_correlate: nb=%d outside [1,16]", nb);
+  DISTIL_CHECK_ARG(phi_snk && phi_src && tau && prof && C, "distil_correlate: null pointer");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  size_t need = 0;
+  distil_correlate_workspace(nt, nv, np, nb, mode, &need);
+  if (nv >= 3 && (ws_bytes < need || !workspace)) {
+    set_error("distil_correlate: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  if (is_mixed(mode))
+    return correlate_mixed(ctx, mode, phi_snk, phi_src, tau, nt, nv, np, prof, nb, prof_per_t, C, workspace,
+                           ws_bytes, s);
+  return correlate_plain(ctx, mode == DISTIL_FP64, phi_snk, phi_src, tau, nt, nv, np, prof, nb, prof_per_t, C,
+                         workspace, ws_bytes, s);
+}
+
+int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, void* lambda,
+                distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(C && lambda, "distil_gevp: null pointer");
+  DISTIL_CHECK_ARG(np >= 1 && nt >= 1, "distil_gevp: np, nt must be >= 1");
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_gevp: nb=%d outside [1,16]", nb);
+  DISTIL_CHECK_ARG(t0 >= 0 && t0 < nt, "distil_gevp: t0=%d outside [0,%d)", t0, nt);
+  return gevp_launch(ctx, C, np, nb, nt, t0, lambda, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_mode_supported(int mode) {
+  if (!valid_mode(mode)) return 0;
+  return is_mixed(mode) ? mixed_mode_built(mode) : 1;
+}
+
+int distil_profile_enable(distil_ctx* ctx, int timing) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  Profiler& p = *ctx->prof;
+  DISTIL_CUDA(cudaDeviceSynchronize());
+  p.reset();
+  p.timing = timing != 0;
+  return DISTIL_OK;
+}
+
+int distil_profile_read(distil_ctx* ctx, distil_kernel_stat* out, int max, int* count) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(count != nullptr && (out != nullptr || max == 0), "distil_profile_read: null pointer");
+  Profiler& p = *ctx->prof;
+  std::vector<double> ms(p.names.size(), 0.0);
+  for (auto& r : p.recs) {
+    DISTIL_CUDA(cudaEventSynchronize(r.b));
+    float f = 0.f;
+    DISTIL_CUDA(cudaEventElapsedTime(&f, r.a, r.b));
+    ms[r.kernel] += f;
+  }
+  int n = (int)p.names.size();
+  *count = n;
+  for (int i = 0; i < n && i < max; ++i) {
+    memset(out[i].name, 0, sizeof(out[i].name));
+    strncpy(out[i].name, p.names[i].c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = p.launches[i];
+    out[i].ms = ms[i];
+  }
+  return DISTIL_OK;
+}
+
+}  // extern "C"

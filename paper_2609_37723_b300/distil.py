@@ -1,0 +1,218 @@
+"""Thin Python binding of libdistil (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the shared library.  PyTorch supplies device memory (tensors are
+passed by ``data_ptr``) and the current CUDA stream.  The functions mirror
+the C interface in ``include/distil.h`` one to one:
+
+    elementals(v, L, mom, mode)                 -> phi   [nt][np][T3]
+    correlate(phi_snk, phi_src, tau, prof, mode) -> C    [np][nb][nb][nt]
+    gevp(C, t0)                                 -> lam   [np][nt][nb]
+
+If the library is missing or cannot be loaded these calls raise; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdistil.so")
+
+FP64, FP32, MIXED_BF16X6, MIXED_BF16X3, MIXED_FP16X3 = 0, 1, 2, 3, 4
+MODE_NAMES = {FP64: "fp64", FP32: "fp32", MIXED_BF16X6: "bf16x6", MIXED_BF16X3: "bf16x3",
+              MIXED_FP16X3: "fp16x3"}
+MODES = {v: k for k, v in MODE_NAMES.items()}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP"}
+
+# Every symbol include/distil.h declares.
+EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
+           "distil_elementals_workspace", "distil_elementals",
+           "distil_correlate_workspace", "distil_correlate", "distil_gevp",
+           "distil_mode_supported", "distil_profile_enable", "distil_profile_read"]
+
+_lib = None
+_ctx = {}
+
+
+class DistilError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"distil {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
+def _declare(L):
+    c_int, c_void_p, c_size_t = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.POINTER
+    L.distil_create.argtypes = [c_int, P(c_void_p)]
+    L.distil_create.restype = c_int
+    L.distil_destroy.argtypes = [c_void_p]
+    L.distil_destroy.restype = None
+    L.distil_last_error.argtypes = []
+    L.distil_last_error.restype = ctypes.c_char_p
+    L.distil_elementals_workspace.argtypes = [c_int, c_int, c_int, c_int, c_int, P(c_size_t)]
+    L.distil_elementals_workspace.restype = c_int
+    L.distil_elementals.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, P(ctypes.c_int32), c_int, c_int,
+                                    c_void_p, c_void_p, c_size_t, c_void_p]
+    L.distil_elementals.restype = c_int
+    L.distil_correlate_workspace.argtypes = [c_int, c_int, c_int, c_int, c_int, P(c_size_t)]
+    L.distil_correlate_workspace.restype = c_int
+    L.distil_correlate.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int,
+                                   c_int, c_int, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.distil_correlate.restype = c_int
+    L.distil_gevp.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
+    L.distil_gevp.restype = c_int
+    L.distil_mode_supported.argtypes = [c_int]
+    L.distil_mode_supported.restype = c_int
+    L.distil_profile_enable.argtypes = [c_void_p, c_int]
+    L.distil_profile_enable.restype = c_int
+    L.distil_profile_read.argtypes = [c_void_p, P(KernelStat), c_int, P(c_int)]
+    L.distil_profile_read.restype = c_int
+
+
+def lib(path: str = LIB_PATH):
+    """Load the shared library (once).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise DistilError(5, f"{path} not built (python -m paper_2609_37723_b300.build)")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().distil_last_error()
+        raise DistilError(status, msg.decode() if msg else "")
+
+
+def context(device: int = 0):
+    if device not in _ctx:
+        h = ctypes.c_void_p()
+        _check(lib().distil_create(device, ctypes.byref(h)))
+        _ctx[device] = h
+    return _ctx[device]
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _mode(mode) -> int:
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def n_triples(nv: int) -> int:
+    return nv * (nv - 1) * (nv - 2) // 6
+
+
+def elementals_workspace(L: int, nt: int, nv: int, np_: int, mode) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().distil_elementals_workspace(L, nt, nv, np_, _mode(mode), ctypes.byref(b)))
+    return b.value
+
+
+def correlate_workspace(nt: int, nv: int, np_: int, nb: int, mode) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().distil_correlate_workspace(nt, nv, np_, nb, _mode(mode), ctypes.byref(b)))
+    return b.value
+
+
+def _workspace(nbytes: int, device):
+    import torch
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def elementals(v, L: int, mom, mode="fp64", out=None, workspace=None, stream=None):
+    """v: [nt][nv][L^3][3] complex tensor on the GPU; mom: [np][3] ints (host)."""
+    import torch
+    mode = _mode(mode)
+    nt, nv = int(v.shape[0]), int(v.shape[1])
+    assert v.is_cuda and v.is_contiguous() and v.shape[2] == L ** 3 and v.shape[3] == 3
+    mom_np = np.ascontiguousarray(np.asarray(mom, dtype=np.int32).reshape(-1, 3))
+    np_ = mom_np.shape[0]
+    cdt = torch.complex128 if mode == FP64 else torch.complex64
+    assert v.dtype == cdt, f"v must be {cdt} for mode {MODE_NAMES[mode]}"
+    if out is None:
+        out = torch.empty((nt, np_, n_triples(nv)), dtype=cdt, device=v.device)
+    ws_bytes = elementals_workspace(L, nt, nv, np_, mode)
+    if workspace is None:
+        workspace = _workspace(ws_bytes, v.device)
+    ctx = context(v.device.index or 0)
+    _check(lib().distil_elementals(ctx, _ptr(v), L, nt, nv,
+                                   mom_np.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), np_, mode,
+                                   _ptr(out), _ptr(workspace) if workspace is not None else None,
+                                   ws_bytes, _stream(stream)))
+    return out
+
+
+def correlate(phi_snk, phi_src, tau, prof, mode="fp64", prof_per_t: bool = False, out=None,
+              workspace=None, stream=None):
+    """phi_snk [nt][np][T3], phi_src [np][T3], tau [nt][4nv][4nv], prof [nb][nv] (f64, GPU)."""
+    import torch
+    mode = _mode(mode)
+    nt, np_ = int(phi_snk.shape[0]), int(phi_snk.shape[1])
+    nv = int(tau.shape[1]) // 4
+    nb = int(prof.shape[-2])
+    assert prof.dtype == torch.float64 and prof.is_cuda and prof.is_contiguous()
+    for x in (phi_snk, phi_src, tau):
+        assert x.is_cuda and x.is_contiguous()
+    if out is None:
+        out = torch.empty((np_, nb, nb, nt), dtype=torch.complex128, device=tau.device)
+    ws_bytes = correlate_workspace(nt, nv, np_, nb, mode)
+    if workspace is None:
+        workspace = _workspace(ws_bytes, tau.device)
+    ctx = context(tau.device.index or 0)
+    _check(lib().distil_correlate(ctx, _ptr(phi_snk), _ptr(phi_src), _ptr(tau), nt, nv, np_, _ptr(prof), nb,
+                                  int(prof_per_t), mode, _ptr(out),
+                                  _ptr(workspace) if workspace is not None else None, ws_bytes,
+                                  _stream(stream)))
+    return out
+
+
+def gevp(C, t0: int, out=None, stream=None):
+    import torch
+    np_, nb, _, nt = (int(s) for s in C.shape)
+    assert C.dtype == torch.complex128 and C.is_cuda and C.is_contiguous()
+    if out is None:
+        out = torch.empty((np_, nt, nb), dtype=torch.complex128, device=C.device)
+    ctx = context(C.device.index or 0)
+    _check(lib().distil_gevp(ctx, _ptr(C), np_, nb, nt, t0, _ptr(out), _stream(stream)))
+    return out
+
+
+def mode_available(mode) -> bool:
+    return bool(lib().distil_mode_supported(_mode(mode)))
+
+
+def profile_enable(timing: bool = False, device: int = 0):
+    """Reset the library's per-kernel launch counters (and event timing)."""
+    _check(lib().distil_profile_enable(context(device), int(timing)))
+
+
+def profile_read(device: int = 0) -> dict:
+    """{kernel family: (launches, summed ms)} since profile_enable()."""
+    n = ctypes.c_int()
+    _check(lib().distil_profile_read(context(device), None, 0, ctypes.byref(n)))
+    arr = (KernelStat * max(1, n.value))()
+    _check(lib().distil_profile_read(context(device), arr, n.value, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(n.value)}

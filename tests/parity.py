@@ -1,0 +1,38 @@
+"""Error measures used by the parity tests.
+
+Correlator entries are gated per entry, e_ab(t) = |C_gpu - C_ref| / |C_ref|;
+an entry whose reference is below 1e-10 of the largest |C(t)| at that
+(p, t) is gated normwise instead (relative to that largest entry).
+"""
+import numpy as np
+
+
+def c_entry_errors(got: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """got, ref: [np][nb][nb][nt] -> per-entry relative errors (same shape)."""
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    scale = np.abs(ref).max(axis=(1, 2), keepdims=True)
+    denom = np.abs(ref)
+    tiny = denom < 1e-10 * scale
+    denom = np.where(tiny, np.maximum(scale, 1e-300), denom)
+    return np.abs(got - ref) / denom
+
+
+def max_c_error(got, ref) -> float:
+    return float(c_entry_errors(got, ref).max())
+
+
+def normwise(got, ref, axis=None) -> float:
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    return float(np.linalg.norm((got - ref).ravel()) / max(np.linalg.norm(ref.ravel()), 1e-300))
+
+
+def phi_error(got, ref) -> float:
+    """Elementals: max over (t, p) of max_r |dPhi| / max_r |Phi| (entries of
+    a random elemental vary over orders of magnitude; a per-(t,p) scale keeps
+    near-zero entries from dominating)."""
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    scale = np.maximum(np.abs(ref).max(axis=-1, keepdims=True), 1e-300)
+    return float((np.abs(got - ref) / scale).max())

@@ -1,0 +1,70 @@
+"""The C-ABI library: it loads, exports every symbol include/distil.h declares,
+and its host-side checks work without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2609_37723_b300 import distil
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "distil.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(distil_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2609_37723_b300 import build
+    if not os.path.exists(distil.LIB_PATH):
+        build.build()
+    return distil.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    syms = header_symbols()
+    assert len(syms) >= 8
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(distil.EXPORTS) <= set(syms)
+
+
+def test_workspace_queries(L):
+    for mode in range(5):
+        b = ctypes.c_size_t()
+        assert L.distil_correlate_workspace(8, 16, 2, 3, mode, ctypes.byref(b)) == 0
+        assert b.value > 0 or mode >= 2
+        assert L.distil_elementals_workspace(8, 8, 16, 2, mode, ctypes.byref(b)) == 0
+    # FP64 needs twice the FP32 bytes for the same intermediates
+    b64, b32 = ctypes.c_size_t(), ctypes.c_size_t()
+    L.distil_correlate_workspace(8, 32, 2, 3, 0, ctypes.byref(b64))
+    L.distil_correlate_workspace(8, 32, 2, 3, 1, ctypes.byref(b32))
+    assert 1.9 < b64.value / b32.value < 2.1
+
+
+def test_bad_arguments_are_rejected(L):
+    b = ctypes.c_size_t()
+    assert L.distil_correlate_workspace(8, 16, 2, 17, 0, ctypes.byref(b)) == 1   # nb > 16
+    assert L.distil_correlate_workspace(8, 16, 2, 3, 9, ctypes.byref(b)) == 1    # bad mode
+    assert b"mode" in L.distil_last_error()
+    assert L.distil_elementals_workspace(0, 8, 16, 2, 0, ctypes.byref(b)) == 1   # L = 0
+    assert L.distil_correlate_workspace(8, 16, 2, 3, 0, None) == 1
+    assert b"null" in L.distil_last_error()
+    # null context: EINVAL, no device touched
+    assert L.distil_gevp(None, None, 1, 1, 1, 0, None, None) == 1
+    assert L.distil_elementals(None, None, 2, 1, 4, None, 1, 0, None, None, 0, None) == 1
+
+
+def test_create_without_gpu_fails_cleanly(L):
+    from conftest import gpu_available
+    if gpu_available():
+        pytest.skip("GPU present")
+    h = ctypes.c_void_p()
+    st = L.distil_create(0, ctypes.byref(h))
+    assert st in (1, 3)
+    assert h.value is None
+    assert len(L.distil_last_error()) > 0
