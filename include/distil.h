@@ -142,6 +142,23 @@ int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0,
                 void* lambda, distil_stream stream);
 
 /* ------------------------------------------------------------------ */
+/* Split-precision complex GEMM (the tensor-core engine on its own)    */
+/* ------------------------------------------------------------------ */
+
+int distil_cgemm_workspace(int M, int N, int K, int batch, int mode, size_t* bytes);
+
+/* C[b][m][n] = sum_k A[b][m][k] * B[b][n][k]  (complex64, no conjugation),
+ * for b < batch, with a tensor-core mode (DISTIL_MIXED_*): both operands are
+ * scaled by powers of two, split into 16-bit pieces and multiplied on
+ * tcgen05 tensor cores with FP32 accumulation.  This is the contraction
+ * engine of distil_correlate; the paper has no separate counterpart (it is
+ * the building block of the mode contractions of Sec. 2.1).
+ *   A [batch][M][K], B [batch][N][K], C [batch][M][N]  c64, device.
+ * Sizes: M, N, K >= 1, 1 <= batch <= 65535.  EINVAL for a CUDA-core mode. */
+int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, int N, int K,
+                 int batch, int mode, void* workspace, size_t ws_bytes, distil_stream stream);
+
+/* ------------------------------------------------------------------ */
 /* Introspection                                                       */
 /* ------------------------------------------------------------------ */
 

@@ -96,7 +96,7 @@ int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv, con
   DISTIL_CHECK_ARG(L >= 1 && L <= EL_MAX_L, "distil_elementals: L=%d outside [1,%d]", L, EL_MAX_L);
   DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1, "distil_elementals: nt, nv, np must be >= 1");
   DISTIL_CHECK_ARG(np <= EL_MAX_MOM, "distil_elementals: at most %d momenta per call", EL_MAX_MOM);
-  DISTIL_CHECK_ARG(v && mom && phi, "distil_elementals: null pointer");
+  DISTIL_CHECK_ARG(mom && ((v && phi) || comb3(nv) == 0), "distil_elementals: null pointer");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (mode == DISTIL_FP64)
     return elementals_simt<double>(ctx, (const Cx<double>*)v, L, nt, nv, mom, np, (Cx<double>*)phi, s);
@@ -129,7 +129,8 @@ int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, 
   DISTIL_CHECK_ARG(valid_mode(mode), "distil_correlate: bad mode %d", mode);
   DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1, "distil_correlate: nt, nv, np must be >= 1");
   DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_correlate: nb=%d outside [1,16]", nb);
-  DISTIL_CHECK_ARG(phi_snk && phi_src && tau && prof && C, "distil_correlate: null pointer");
+  DISTIL_CHECK_ARG(tau && prof && C && ((phi_snk && phi_src) || comb3(nv) == 0),
+                   "distil_correlate: null pointer");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   size_t need = 0;
   distil_correlate_workspace(nt, nv, np, nb, mode, &need);
@@ -153,6 +154,30 @@ int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, 
   DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_gevp: nb=%d outside [1,16]", nb);
   DISTIL_CHECK_ARG(t0 >= 0 && t0 < nt, "distil_gevp: t0=%d outside [0,%d)", t0, nt);
   return gevp_launch(ctx, C, np, nb, nt, t0, lambda, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_cgemm_workspace(int M, int N, int K, int batch, int mode, size_t* bytes) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
+  DISTIL_CHECK_ARG(is_mixed(mode), "distil_cgemm: mode %d is not a tensor-core mode", mode);
+  DISTIL_CHECK_ARG(M >= 1 && N >= 1 && K >= 1 && batch >= 1, "bad sizes");
+  *bytes = cgemm_workspace(mode, M, N, K, batch);
+  return DISTIL_OK;
+}
+
+int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, int N, int K, int batch, int mode,
+                 void* workspace, size_t ws_bytes, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(is_mixed(mode), "distil_cgemm: mode %d is not a tensor-core mode", mode);
+  DISTIL_CHECK_ARG(M >= 1 && N >= 1 && K >= 1 && batch >= 1 && batch <= 65535, "distil_cgemm: bad sizes");
+  DISTIL_CHECK_ARG(A && B && C && workspace, "distil_cgemm: null pointer");
+  size_t need = cgemm_workspace(mode, M, N, K, batch);
+  if (ws_bytes < need) {
+    set_error("distil_cgemm: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  return cgemm_mixed(ctx, mode, A, B, C, M, N, K, batch, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int distil_mode_supported(int mode) {

@@ -14,4 +14,8 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
                     int nv, int np, const double* prof, int nb, int prof_per_t, void* C, void* ws,
                     size_t ws_bytes, cudaStream_t s);
 
+size_t cgemm_workspace(int mode, long long M, long long N, long long K, long long batch);
+int cgemm_mixed(distil_ctx* ctx, int mode, const void* A, const void* B, void* C, int M, int N, int K, int batch,
+                void* ws, size_t ws_bytes, cudaStream_t s);
+
 }  // namespace distil

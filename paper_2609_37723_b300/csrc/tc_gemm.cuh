@@ -1,0 +1,189 @@
+// Split-precision complex GEMM on tcgen05 tensor cores.
+//
+//   D[b](m, n) = sum_k A[b](m, k) * B[b](n, k)          (complex, FP32 accumulate)
+//
+// A and B arrive pre-split: each complex operand is a stack of 2*NP real
+// 16-bit planes (piece p, re/im), K contiguous, read by TMA with the swizzle
+// that matches the K-chunk (32/64/128-byte rows).  For every K step and every
+// product (pa, pb) of the split scheme four MMAs update two TMEM accumulators:
+//   D_re += A_re[pa] B_re[pb] + (-A_im[pa]) B_im[pb]   (negate-A descriptor)
+//   D_im += A_re[pa] B_im[pb] + A_im[pa] B_re[pb]
+// One CTA computes a 128 x NT tile: warp 0 issues TMA loads into a STAGES-deep
+// ring, warp 1 allocates TMEM and issues the MMAs, warps 2..5 read the
+// accumulators back (tcgen05.ld) and hand 16-column slices to the epilogue
+// functor.  All waits are bounded (tc.cuh).
+#pragma once
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace distil {
+namespace tc {
+
+struct OpMap {
+  int bdiv, bmod;  // operand batch coordinate = ((batch / bdiv) % bmod) * bmul + badd
+  int bmul, badd;
+  int row_off;     // added to the tile's first row
+  __device__ __forceinline__ int coord(int batch) const { return ((batch / bdiv) % bmod) * bmul + badd; }
+};
+
+struct GemmCfg {
+  int M, N, K;
+  OpMap a, b;
+  int nprod;
+  int pa[6], pb[6];
+  unsigned* err;
+};
+
+template <int NT, int KC, int NPL>
+struct TileGeom {
+  static constexpr int SWZ = KC * 2;                  // bytes per tile row
+  static constexpr int A_PLANE = 128 * SWZ;
+  static constexpr int B_PLANE = NT * SWZ;
+  static constexpr int A_STAGE = NPL * A_PLANE;
+  static constexpr int B_STAGE = NPL * B_PLANE;
+  static constexpr int STAGE = A_STAGE + B_STAGE;
+};
+
+template <int NT, int KC, int NPL, int STAGES>
+constexpr size_t gemm_smem_bytes() {
+  return (size_t)STAGES * TileGeom<NT, KC, NPL>::STAGE + 1024 /*align*/ + 256 /*barriers*/;
+}
+
+template <int NT, int KC, int NPL, int STAGES, bool BF16, class Epi>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   GemmCfg cfg, Epi epi) {
+  using G = TileGeom<NT, KC, NPL>;
+  static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "N tile");
+  static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * G::A_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * G::B_STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint32_t* abort_flag = tslot + 1;
+  uint32_t* issued_s = tslot + 2;
+
+  // a CTA of a launch that already hit a timeout does nothing
+  if (cfg.err && *(volatile unsigned*)cfg.err) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y, batch = blockIdx.z;
+  const int nk = (cfg.K + KC - 1) / KC;
+  constexpr uint32_t TCOLS = 2 * NT;  // D_re | D_im
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *abort_flag = 0;
+    *issued_s = 0;
+    fence_mbar_init();
+    tma_prefetch(&mapA);
+    tma_prefetch(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, TCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    const int ca = cfg.a.coord(batch);
+    const int cb = cfg.b.coord(batch);
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT) || *(volatile uint32_t*)abort_flag) {
+        *(volatile uint32_t*)abort_flag = 1;
+        break;
+      }
+      mbar_arrive_expect_tx(&full[s], G::STAGE);
+      tma_load_4d(&mapA, &full[s], sA + s * G::A_STAGE, kb * KC, m_tile * 128 + cfg.a.row_off, 0, ca);
+      tma_load_4d(&mapB, &full[s], sB + s * G::B_STAGE, kb * KC, n_tile * NT + cfg.b.row_off, 0, cb);
+      ++issued;
+    }
+    *(volatile uint32_t*)issued_s = issued;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    const uint32_t id = idesc_f16(128, NT, BF16, false);
+    const uint32_t idn = idesc_f16(128, NT, BF16, true);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *(volatile uint32_t*)abort_flag) {
+        *(volatile uint32_t*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * G::A_STAGE);
+      const uint32_t b0 = smem_u32(sB + s * G::B_STAGE);
+#pragma unroll
+      for (int ks = 0; ks < KC / 16; ++ks) {
+        for (int p = 0; p < cfg.nprod; ++p) {
+          const uint32_t ar = a0 + (2 * cfg.pa[p]) * G::A_PLANE + ks * 32;
+          const uint32_t ai = ar + G::A_PLANE;
+          const uint32_t br = b0 + (2 * cfg.pb[p]) * G::B_PLANE + ks * 32;
+          const uint32_t bi = br + G::B_PLANE;
+          const uint64_t dar = smem_desc(ar, G::SWZ), dai = smem_desc(ai, G::SWZ);
+          const uint64_t dbr = smem_desc(br, G::SWZ), dbi = smem_desc(bi, G::SWZ);
+          const uint32_t acc = (kb > 0 || ks > 0 || p > 0) ? 1u : 0u;
+          mma_f16(tmem, dar, dbr, id, acc);
+          mma_f16(tmem, dai, dbi, idn, 1u);
+          mma_f16(tmem + NT, dar, dbi, id, acc);
+          mma_f16(tmem + NT, dai, dbr, id, 1u);
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accf);  // fires once every MMA above has completed (also on abort)
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    bool ok = mbar_wait(accf, 0, cfg.err, TC_ERR_ACC_WAIT);
+    ok = __all_sync(0xffffffffu, ok && !*(volatile uint32_t*)abort_flag);  // warp-uniform for tcgen05.ld
+    tc_fence_after();
+    if (ok) {
+      const int row = m_tile * 128 + q * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < NT / 16; ++c) {
+        uint32_t re[16], im[16];
+        tmem_ld16(tl + c * 16, re);
+        tmem_ld16(tl + NT + c * 16, im);
+        tmem_wait_ld();
+        if (row < cfg.M) epi(batch, row, n_tile * NT + c * 16, reinterpret_cast<const float*>(re),
+                             reinterpret_cast<const float*>(im));
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *(volatile uint32_t*)abort_flag) {
+    // drain: wait (bounded) for the last load of every stage, so no copy
+    // lands in shared memory after the CTA has exited
+    const int issued = *(volatile uint32_t*)issued_s;
+    for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+      if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+}  // namespace tc
+}  // namespace distil

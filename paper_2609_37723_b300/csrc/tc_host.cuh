@@ -1,0 +1,57 @@
+// Host side of the tensor-core GEMM: TMA tensor maps for stacks of 16-bit
+// planes and the launch wrapper of tc_gemm_kernel.
+#pragma once
+#include <cuda.h>
+
+#include "common.cuh"
+#include "prof.cuh"
+#include "tc_gemm.cuh"
+
+namespace distil {
+namespace tc {
+
+// A stack of 16-bit planes: element (k, row, plane, batch) at
+// base + batch*batch_stride + plane*plane_stride + row*ld + k  (elements).
+struct Planes {
+  void* base;
+  long long K, rows, planes, batch;
+  long long ld, plane_stride, batch_stride;
+};
+
+inline long long pad64(long long k) { return (k + 63) / 64 * 64; }
+
+int encode_planes(CUtensorMap* map, const Planes& t, int box_rows, int kc, bool bf16);
+
+template <int NT, int KC, int NPL, int STAGES, bool BF16, class Epi>
+int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg,
+                int batch, const Epi& epi, cudaStream_t s) {
+  if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
+  if (cfg.K <= 0) {
+    set_error("%s: K must be positive", name);
+    return DISTIL_EINVAL;
+  }
+  CUtensorMap ma, mb;
+  DISTIL_TRY(encode_planes(&ma, A, 128, KC, BF16));
+  DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
+  constexpr size_t smem = gemm_smem_bytes<NT, KC, NPL, STAGES>();
+  auto kern = tc_gemm_kernel<NT, KC, NPL, STAGES, BF16, Epi>;
+  static bool attr = false;
+  if (!attr) {
+    DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid((unsigned)((cfg.N + NT - 1) / NT), (unsigned)((cfg.M + 127) / 128), (unsigned)batch);
+  if (grid.y > 65535 || grid.z > 65535) {
+    set_error("%s: grid too large", name);
+    return DISTIL_EINVAL;
+  }
+  {
+    Launch L(ctx, name, s);
+    kern<<<grid, 192, smem, s>>>(ma, mb, cfg, epi);
+  }
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
+}  // namespace tc
+}  // namespace distil

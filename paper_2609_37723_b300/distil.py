@@ -33,6 +33,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOT
 EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_elementals_workspace", "distil_elementals",
            "distil_correlate_workspace", "distil_correlate", "distil_gevp",
+           "distil_cgemm_workspace", "distil_cgemm",
            "distil_mode_supported", "distil_profile_enable", "distil_profile_read"]
 
 _lib = None
@@ -70,6 +71,11 @@ def _declare(L):
     L.distil_correlate.restype = c_int
     L.distil_gevp.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
     L.distil_gevp.restype = c_int
+    L.distil_cgemm_workspace.argtypes = [c_int, c_int, c_int, c_int, c_int, P(c_size_t)]
+    L.distil_cgemm_workspace.restype = c_int
+    L.distil_cgemm.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int,
+                               c_void_p, c_size_t, c_void_p]
+    L.distil_cgemm.restype = c_int
     L.distil_mode_supported.argtypes = [c_int]
     L.distil_mode_supported.restype = c_int
     L.distil_profile_enable.argtypes = [c_void_p, c_int]
@@ -186,6 +192,26 @@ def correlate(phi_snk, phi_src, tau, prof, mode="fp64", prof_per_t: bool = False
                                   int(prof_per_t), mode, _ptr(out),
                                   _ptr(workspace) if workspace is not None else None, ws_bytes,
                                   _stream(stream)))
+    return out
+
+
+def cgemm(A, B, mode="fp16x3", out=None, workspace=None, stream=None):
+    """C[b] = A[b] @ B[b]^T (complex64, tensor cores, split pieces)."""
+    import torch
+    mode = _mode(mode)
+    if A.dim() == 2:
+        A, B = A[None], B[None]
+    batch, M, K = (int(s) for s in A.shape)
+    N = int(B.shape[1])
+    assert A.dtype == torch.complex64 and B.dtype == torch.complex64 and A.is_contiguous() and B.is_contiguous()
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=torch.complex64, device=A.device)
+    b = ctypes.c_size_t()
+    _check(lib().distil_cgemm_workspace(M, N, K, batch, mode, ctypes.byref(b)))
+    if workspace is None:
+        workspace = _workspace(b.value, A.device)
+    _check(lib().distil_cgemm(context(A.device.index or 0), _ptr(A), _ptr(B), _ptr(out), M, N, K, batch, mode,
+                              _ptr(workspace), b.value, _stream(stream)))
     return out
 
 
