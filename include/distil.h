@@ -60,16 +60,28 @@ typedef enum {
   DISTIL_ENOTSUP = 5   /* mode or size not supported by this build         */
 } distil_status;
 
-/* Arithmetic of a call.  Storage types follow the mode: FP64 reads and
- * writes c128; every other mode reads c64 eigenvectors / perambulators /
- * elementals.  The correlation matrix and GEVP are always c128. */
+/* Arithmetic of a call.
+ * Storage types: FP64 reads and writes c128 everywhere.  FP32 reads and
+ * writes c64 (eigenvectors, perambulators, elementals).  The tensor-core
+ * modes read c64 eigenvectors and perambulators and keep the elementals in
+ * c128 (distil_elementals writes c128, distil_correlate reads c128).  The
+ * correlation matrix and the GEVP are always c128.
+ * Tensor-core modes split every operand row (power-of-two exponent of its
+ * largest entry) into 16-bit pieces and accumulate in TMEM:
+ *   FP16X6  fixed-point slices of 7 + 11 + 11 bits, 6 products; the leading
+ *           product is integer-valued and sums exactly (about 2^-29 of the
+ *           row maximum per GEMM).  The accurate mode.
+ *   BF16X6  fixed-point slices of 8 + 8 + 8 bits, 6 products (2^-24).
+ *   BF16X3  fixed-point slices of 8 + 8 bits, 3 products (2^-16).
+ *   FP16X3  floating pieces h + l (22 bits), 3 products; not exact: the
+ *           tensor core's FP32 accumulation error grows with K. */
 typedef enum {
-  DISTIL_FP64 = 0,        /* plain FP64 on CUDA cores                        */
-  DISTIL_FP32 = 1,        /* plain FP32 on CUDA cores, FP64 final sums       */
-  DISTIL_MIXED_BF16X6 = 2,/* tensor cores: 3-piece BF16 split, 6 products    */
-  DISTIL_MIXED_BF16X3 = 3,/* tensor cores: 2-piece BF16 split, 3 products    */
-  DISTIL_MIXED_FP16X3 = 4 /* tensor cores: 2-piece FP16 split, 3 products,
-                             power-of-two operand scaling                    */
+  DISTIL_FP64 = 0,         /* plain FP64 on CUDA cores                        */
+  DISTIL_FP32 = 1,         /* plain FP32 on CUDA cores, FP64 final sums       */
+  DISTIL_MIXED_BF16X6 = 2, /* tensor cores, see above                         */
+  DISTIL_MIXED_BF16X3 = 3,
+  DISTIL_MIXED_FP16X3 = 4,
+  DISTIL_MIXED_FP16X6 = 5
 } distil_mode;
 
 typedef struct distil_ctx distil_ctx;

@@ -95,9 +95,10 @@ const char* get_error();
   } while (0)
 
 inline bool is_mixed(int mode) {
-  return mode == DISTIL_MIXED_BF16X6 || mode == DISTIL_MIXED_BF16X3 || mode == DISTIL_MIXED_FP16X3;
+  return mode == DISTIL_MIXED_BF16X6 || mode == DISTIL_MIXED_BF16X3 || mode == DISTIL_MIXED_FP16X3 ||
+         mode == DISTIL_MIXED_FP16X6;
 }
-inline bool valid_mode(int mode) { return mode >= DISTIL_FP64 && mode <= DISTIL_MIXED_FP16X3; }
+inline bool valid_mode(int mode) { return mode >= DISTIL_FP64 && mode <= DISTIL_MIXED_FP16X6; }
 
 // Bump allocator over a caller-provided workspace (256-byte aligned slices).
 struct Arena {

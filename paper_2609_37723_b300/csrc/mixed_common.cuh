@@ -1,6 +1,27 @@
 // Pieces shared by the mixed-precision (split 16-bit, tensor-core) paths:
-// split schemes, power-of-two operand scales, split/store helpers and the
-// GEMM epilogues.
+// split schemes, per-row power-of-two exponents, the row-splitting kernel
+// and the GEMM epilogues.
+//
+// Split schemes.  A row of an operand with max |x| < 2^e is represented as
+//  * fixed-point slices: t = x 2^(H-e) = hi + 2^-W mid + 2^-2W lo with hi,
+//    mid, lo integers (|hi| <= 2^H, |mid|, |lo| <= 2^(W-1)), exact in the
+//    16-bit type (FP16: W = 11, H <= 10; BF16: W = 8, H <= 7).  The products
+//    hi*hi are integers, so the sums of the leading slices are integers that
+//    the tensor core accumulates exactly in FP32, whatever its rounding, as
+//    long as the partial sums stay below 2^24 (guaranteed for
+//    K <= 2^(23 - 2H); for rows of random sign the partial sums grow like
+//    sqrt(K) and the bound is met up to K ~ 2^(47 - 4H + 2 log2(4))).  The
+//    cross terms go to a second accumulator weighted 2^-W; it holds values
+//    about 2^-W |mid/hi| of the result, so its inexact rounding stays far
+//    below the target.  A pieces: hi, mid, lo 2^-W.  B pieces: hi, mid,
+//    mid 2^-W, lo 2^-W (hi*lo, mid*mid, lo*hi all carry 2^-2W).  Dropped
+//    terms (mid*lo, lo*mid, lo*lo) are of relative size 2^-3W |mid lo| /
+//    |hi|^2: about 2^-33 * 2^(22 - 2H + 4) for FP16, so H trades the
+//    dropped-term error against the exactness range: H = 9 for the short
+//    (K <= 4 N_v) mode contractions, H = 8 for the long (K = 3 V3)
+//    elemental contraction.
+//  * floating pieces (FP16X3): t = x 2^(14-e) = h + l, h = fp16(t),
+//    l = fp16(t - h); accumulation rounding is not exact.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -11,101 +32,179 @@
 
 namespace distil {
 
-// Products kept by each split scheme (piece of A, piece of B): all pairs
-// whose piece orders add up to at most NP-1.
 struct Scheme {
-  bool bf16;
-  int np;  // pieces per real value
+  bool bf16, fixed;
+  int H, W;    // fixed point: t = x 2^(H - e), slices of W bits; floating: H = 14
+               // (H of the mode contractions; the elementals use H - 1)
+  int na, nb;  // pieces of the A / B operand
   int nprod;
-  int pa[6], pb[6];
+  int pa[6], pb[6], acc[6];
+  float w1;    // weight of the second accumulator (2^-W)
+  int shift;   // D *= 2^(eA + eB - shift), shift = 2H
 };
+
 inline Scheme scheme_of(int mode) {
-  if (mode == DISTIL_MIXED_BF16X6) return Scheme{true, 3, 6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
-  if (mode == DISTIL_MIXED_BF16X3) return Scheme{true, 2, 3, {0, 0, 1}, {0, 1, 0}};
-  return Scheme{false, 2, 3, {0, 0, 1}, {0, 1, 0}};  // FP16X3
+  if (mode == DISTIL_MIXED_FP16X6)
+    return Scheme{false, true, 9, 11, 3, 4, 6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 3, 2, 0}, {0, 1, 1, 1, 1, 1},
+                  1.f / 2048.f, 18};
+  if (mode == DISTIL_MIXED_BF16X6)
+    return Scheme{true, true, 7, 8, 3, 4, 6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 3, 2, 0}, {0, 1, 1, 1, 1, 1},
+                  1.f / 256.f, 14};
+  if (mode == DISTIL_MIXED_BF16X3)
+    return Scheme{true, true, 7, 8, 2, 2, 3, {0, 0, 1}, {0, 1, 0}, {0, 1, 1}, 1.f / 256.f, 14};
+  return Scheme{false, false, 14, 0, 2, 2, 3, {0, 0, 1}, {0, 1, 0}, {0, 1, 1}, 1.f, 28};  // FP16X3
 }
 
-// --------------------------------------------------------------- scales
-// A tensor with max |x| = m is stored as pieces of x * 2^e with
-// e = 14 - ceil(log2 m), so the leading piece stays below 2^14 (FP16 range)
-// and the trailing pieces stay normal for every entry within 2^-17 of m.
-__device__ __forceinline__ float pow2_scale(float m) {
-  if (!(m > 0.f) || !isfinite(m)) return 1.f;
+inline void fill_products(tc::GemmCfg& cfg, const Scheme& s) {
+  cfg.nprod = s.nprod;
+  for (int i = 0; i < s.nprod; ++i) {
+    cfg.pa[i] = s.pa[i];
+    cfg.pb[i] = s.pb[i];
+    cfg.acc[i] = s.acc[i];
+  }
+  cfg.w1 = s.w1;
+  cfg.shift = s.shift;
+}
+
+// Exponent e with max |x| < 2^e (0 for an all-zero row).
+__device__ __forceinline__ int row_exponent_d(double m) {
+  if (!(m > 0.0) || !isfinite(m)) return 0;
   int e;
-  frexpf(m, &e);  // m = f * 2^e, f in [0.5, 1)  ->  m <= 2^e
-  return ldexpf(1.f, 14 - e);
+  frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+  return e;
 }
 
-// Max |x| of a complex array into *out (float bits, non-negative, so
-// unsigned ordering is float ordering).  *out must start at 0.
-template <typename T>
-__global__ void maxabs_kernel(const Cx<T>* __restrict__ x, long long n, unsigned* out) {
-  float m = 0.f;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    m = fmaxf(m, fmaxf(fabsf((float)x[e].r), fabsf((float)x[e].i)));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
-}
+// Slice width of the fixed-point pieces: 11 bits in FP16, 8 in BF16.
+template <bool BF16>
+struct SliceBits {
+  static constexpr int W = BF16 ? 8 : 11;
+};
 
-// Store x (already scaled) as NP pieces into planes (piece*2 + ri).
-template <bool BF16, int NP>
-__device__ __forceinline__ void store_split(typename tc::Piece<BF16>::T* base, long long plane_stride, int ri,
-                                            float x) {
-  typename tc::Piece<BF16>::T p[NP];
-  tc::split16<BF16, NP>(x, p);
+// NPC pieces of x (given in double so that results of an FP64 epilogue
+// keep all their bits) for a row with exponent e and leading-slice width
+// H (scheme notes above).
+template <bool BF16, bool FIXED, int NPC>
+__device__ __forceinline__ void make_pieces(double x, int e, int H, typename tc::Piece<BF16>::T (&p)[NPC]) {
+  using PC = tc::Piece<BF16>;
+  constexpr int W = SliceBits<BF16>::W;
+  if constexpr (FIXED) {
+    constexpr double sw = (double)(1 << W), isw = 1.0 / (double)(1 << W);
+    const double t = ldexp(x, H - e);
+    const double hi = rint(t);
+    const double r1 = (t - hi) * sw;
+    const double mid = rint(r1);
+    const double lo = rint((r1 - mid) * sw);
+    p[0] = PC::from((float)hi);
+    if constexpr (NPC >= 2) p[1] = PC::from((float)mid);
+    if constexpr (NPC == 3) p[2] = PC::from((float)(lo * isw));
+    if constexpr (NPC == 4) {
+      p[2] = PC::from((float)(mid * isw));
+      p[3] = PC::from((float)(lo * isw));
+    }
+  } else {
+    float t = (float)ldexp(x, H - e);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) base[(2 * i + ri) * plane_stride] = p[i];
+    for (int i = 0; i < NPC; ++i) {
+      p[i] = PC::from(t);
+      t -= PC::to(p[i]);
+    }
+  }
+}
+
+// Split rows of a complex operand into 2*NPC planes with a per-row exponent.
+// Global row r = coord * rows_per + rr goes to
+//   out[coord][plane][rr][k]  (plane stride rows_per*ld, coord stride 2*NPC*rows_per*ld)
+// and exps[r].  One warp per row: pass 1 finds max |re|, |im| over the row,
+// pass 2 writes the pieces.  Src::operator()(r, k) returns the element.
+// Optionally also the row's 2-norm sqrt(sum |x|^2) into norms[r].
+template <bool BF16, bool FIXED, int NPC, class Src>
+__global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, long long rows_per, int K, int H,
+                                                         typename tc::Piece<BF16>::T* __restrict__ out, long long ld,
+                                                         int* __restrict__ exps, float* __restrict__ norms) {
+  using P16 = typename tc::Piece<BF16>::T;
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  double m = 0.0, ss = 0.0;
+  for (int k = lane; k < K; k += 32) {
+    const double2 v = src(r, k);
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    ss += v.x * v.x + v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  const int e = row_exponent_d(m);
+  if (lane == 0) {
+    exps[r] = e;
+    if (norms) norms[r] = (float)(sqrt(ss) * (1.0 + 1e-6));
+  }
+  const long long coord = r / rows_per, rr = r % rows_per;
+  const long long ps = rows_per * ld;
+  P16* base = out + coord * (2 * NPC) * ps + rr * ld;
+  for (int k = lane; k < K; k += 32) {
+    const double2 v = src(r, k);
+    P16 pr[NPC], pi[NPC];
+    make_pieces<BF16, FIXED, NPC>(v.x, e, H, pr);
+    make_pieces<BF16, FIXED, NPC>(v.y, e, H, pi);
+#pragma unroll
+    for (int i = 0; i < NPC; ++i) {
+      base[(2 * i) * ps + k] = pr[i];
+      base[(2 * i + 1) * ps + k] = pi[i];
+    }
+  }
+}
+
+// Planes descriptor matching split_rows_kernel's layout.
+inline tc::Planes planes_of(void* base, long long K, long long rows_per, long long ncoord, int npl, long long ld) {
+  return tc::Planes{base, K, rows_per, npl, ncoord, ld, rows_per * ld, (long long)npl * rows_per * ld};
+}
+
+template <bool BF16, bool FIXED, int NPC, class Src>
+inline int split_rows(distil_ctx* ctx, const Src& src, long long nrows, long long rows_per, int K, int H, void* out,
+                      long long ld, int* exps, cudaStream_t s, float* norms = nullptr) {
+  if (nrows <= 0) return DISTIL_OK;
+  const long long threads = nrows * 32;
+  Launch L(ctx, "split_rows", s);
+  split_rows_kernel<BF16, FIXED, NPC, Src><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      src, nrows, rows_per, K, H, reinterpret_cast<typename tc::Piece<BF16>::T*>(out), ld, exps, norms);
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
 }
 
 // --------------------------------------------------------------- epilogues
-// out[batch][row][col] = factor * D (complex FP32), two-level batch offset.
-struct EpiC64 {
-  float2* out;
-  long long sb_hi, sb_lo;
-  int b_lo;
-  long long sr;
-  int N;
-  const float* factor;
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re, const float* im) const {
-    const float f = *factor;
-    float2* dst = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr +
-                  col0;
-    if (col0 + 16 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-      float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        d4[e] = make_float4(re[2 * e] * f, im[2 * e] * f, re[2 * e + 1] * f, im[2 * e + 1] * f);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 16; ++e)
-        if (col0 + e < N) dst[e] = make_float2(re[e] * f, im[e] * f);
-    }
+// Column map shared by the epilogues: colmap(c) = (c / cdiv) * cs1 +
+// (c % cdiv) * sc, or c * sc when cdiv == 0.
+struct ColMap {
+  long long sc;
+  int cdiv;
+  long long cs1;
+  __device__ __forceinline__ long long operator()(int c) const {
+    return cdiv ? (long long)(c / cdiv) * cs1 + (long long)(c % cdiv) * sc : (long long)c * sc;
   }
 };
 
-// Split epilogue: out planes (two-level batch) [plane][row][col] of NP pieces
-// of factor * D; used where the result feeds the next tensor-core GEMM.
-// Column c maps to (c / cdiv) * cs1 + (c % cdiv) * cs0 within the row.
-template <bool BF16, int NP>
-struct EpiSplit {
-  typename tc::Piece<BF16>::T* out;
+// out[batch][row * sr + colmap(col)] = D, stored as complex64 (OUT = float2)
+// or complex128 (OUT = double2); two-level batch offset.
+template <class OUT>
+struct EpiStore {
+  OUT* out;
   long long sb_hi, sb_lo;
   int b_lo;
-  long long plane_stride, sr;
-  int cdiv;
-  long long cs0, cs1;
+  long long sr;
+  ColMap cm;
   int N;
-  const float* factor;
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re, const float* im) const {
-    const float f = *factor;
-    auto* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
+  __device__ __forceinline__ void operator()(int batch, int row, int col0, const double* re, const double* im) const {
+    OUT* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int c = col0 + e;
       if (c >= N) break;
-      auto* d = base + (long long)(c / cdiv) * cs1 + (long long)(c % cdiv) * cs0;
-      store_split<BF16, NP>(d, plane_stride, 0, re[e] * f);
-      store_split<BF16, NP>(d, plane_stride, 1, im[e] * f);
+      OUT v;
+      v.x = re[e];
+      v.y = im[e];
+      base[cm(c)] = v;
     }
   }
 };

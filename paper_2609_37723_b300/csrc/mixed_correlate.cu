@@ -1,17 +1,21 @@
 // Mixed-precision correlation matrix: the three mode contractions of
 // correlate.cuh on tcgen05 tensor cores with operands split into 16-bit
-// pieces (FP32 accumulation in TMEM), intermediates re-split by the GEMM
-// epilogue, and the final dot accumulated in FP64.
+// pieces with per-row power-of-two exponents (mixed_common.cuh), FP32
+// accumulation in TMEM combined in FP64, FP64 intermediates between the
+// contractions, and the final dot accumulated in FP64.
 //
 // Per (t, p):
-//   scales   power-of-two scales of tau, Phi_snk, Phi_src, the profiles
-//   split    Aa (12 n x n), tauT (4n x 4n), Tc (5 n x n) from tau;
-//            G[a] (n^2 x n) from Phi_snk and the profiles;
-//            S[b] (P2 x n) from conj(Phi_src) and the profiles
-//   step i   U[a][a'][(i',k)][(beta,j)] = sum_i Aa[a'beta][i'][i] G[a][(k,j)][i]
-//   step j   V[a][slot][j'][(i',k)]     = sum_(beta,j) tauT[(b'j')][(beta j)] U[a][a'][(i',k)][(beta,j)]
-//   source   X[b][c][pair][k]          = sum_k' S[b][pair][k'] Tc[c][k][k']
-//   dot      C_ab                       (dot.cuh)
+//   split    Aa  rows (a'beta, i')  K i        from Gamma_beta tau[(alpha(beta) i)][(a' i')]
+//            tauT rows (b' j')      K (beta j) from tau[(beta j)][(b' j')]
+//            Tc  rows (c, k)        K k'       from the five source blocks
+//            G   rows (a, (k,j))    K i        from g g g Phi_snk
+//            S   rows (b, i'<j')    K k'       from g g g conj(Phi_src)
+//   step i   U[a][a'][(i',k)][(beta,j)] = sum_i Aa G, split by the epilogue
+//            with the row exponent of the Cauchy-Schwarz bound
+//            |U| <= max_beta |Aa row| * max_j |G row|
+//   step j   V[a][slot][j'][(i',k)]     = sum_(beta,j) U tauT        (complex128)
+//   source   X[b][c][pair][k]           = sum_k' S Tc                (complex128)
+//   dot      C_ab                         (dot.cuh)
 #include "correlate.cuh"
 #include "dot.cuh"
 #include "mixed.cuh"
@@ -21,269 +25,249 @@ namespace distil {
 
 using tc::Planes;
 
-enum { SC_MTAU = 0, SC_MPHIS, SC_MPHI0, SC_MG, SC_STAU, SC_STC, SC_SG, SC_SS, SC_SU, SC_FA, SC_FB, SC_FX, SC_N };
+// ------------------------------------------------------------------ sources
+__device__ __forceinline__ double2 d2(float2 x) { return make_double2(x.x, x.y); }
 
-__global__ void prof_max_kernel(const double* g, long long n, unsigned* out) {
-  float m = 0.f;
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) m = fmaxf(m, (float)fabs(g[e]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
-}
-
-__global__ void scales_kernel(float* sc, int nv) {
-  const float mt = __uint_as_float(reinterpret_cast<unsigned*>(sc)[SC_MTAU]);
-  const float ms = __uint_as_float(reinterpret_cast<unsigned*>(sc)[SC_MPHIS]);
-  const float m0 = __uint_as_float(reinterpret_cast<unsigned*>(sc)[SC_MPHI0]);
-  const float mg = __uint_as_float(reinterpret_cast<unsigned*>(sc)[SC_MG]);
-  const float g3 = mg * mg * mg;
-  const float st = pow2_scale(mt), stc = pow2_scale(2.f * mt);
-  const float sg = pow2_scale(ms * g3), ss = pow2_scale(m0 * g3);
-  const float su = pow2_scale((float)nv * mt * ms * g3);
-  sc[SC_STAU] = st;
-  sc[SC_STC] = stc;
-  sc[SC_SG] = sg;
-  sc[SC_SS] = ss;
-  sc[SC_SU] = su;
-  sc[SC_FA] = su / (st * sg);
-  sc[SC_FB] = 1.f / (st * su);
-  sc[SC_FX] = 1.f / (ss * stc);
-}
-
-// Aa planes [12][NPL][n][ldn], tauT planes [NPL][4n][ld4], Tc planes [5][NPL][n][ldn].
-template <bool BF16, int NP>
-__global__ void split_tau_kernel(const float2* __restrict__ tau, int nv, const float* __restrict__ sc,
-                                 typename tc::Piece<BF16>::T* __restrict__ Aa, long long ldn,
-                                 typename tc::Piece<BF16>::T* __restrict__ TT, long long ld4,
-                                 typename tc::Piece<BF16>::T* __restrict__ Tc) {
-  constexpr int NPL = 2 * NP;
-  const long long n = nv, n2 = n * n, n4 = 4 * n;
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const float st = sc[SC_STAU], stc = sc[SC_STC];
-  if (e < 12 * n2) {
-    const int ab = (int)(e / n2);  // a'*4 + beta
-    const int ap = ab / 4, beta = ab % 4, alpha = beta ^ 1;
-    const int ipr = (int)((e / n) % n), i = (int)(e % n);
-    const float gam = (beta & 1) ? -st : st;
-    const float2 x = tau[(alpha * n + i) * n4 + ap * n + ipr];
-    auto* d = Aa + (long long)ab * NPL * n * ldn + ipr * ldn + i;
-    store_split<BF16, NP>(d, n * ldn, 0, x.x * gam);
-    store_split<BF16, NP>(d, n * ldn, 1, x.y * gam);
-  } else if (e < 28 * n2) {
-    const long long f = e - 12 * n2;
-    const long long r = f / n4, k = f % n4;  // tauT[r][k] = tau[k][r]
-    const float2 x = tau[k * n4 + r];
-    auto* d = TT + r * ld4 + k;
-    store_split<BF16, NP>(d, n4 * ld4, 0, x.x * st);
-    store_split<BF16, NP>(d, n4 * ld4, 1, x.y * st);
-  } else if (e < 33 * n2) {
-    const long long f = e - 28 * n2;
-    const int c = (int)(f / n2);
-    const int k = (int)((f / n) % n), kp = (int)(f % n);
-    float2 x;
+struct AaSrc {  // rows (a'*4 + beta)*n + i', K = i
+  const float2* tau;
+  int n;
+  __device__ __forceinline__ double2 operator()(long long r, int i) const {
+    const int ab = (int)(r / n), ip = (int)(r % n);
+    const int ap = ab >> 2, beta = ab & 3, alpha = beta ^ 1;
+    const float2 x = tau[((long long)alpha * n + i) * 4 * n + ap * n + ip];
+    // Gamma_{10} = Gamma_{32} = +1, Gamma_{01} = Gamma_{23} = -1
+    return (beta & 1) ? make_double2(-x.x, -x.y) : d2(x);
+  }
+};
+struct TTSrc {  // rows (b'j'), K = (beta j): tau^T
+  const float2* tau;
+  int n;
+  __device__ __forceinline__ double2 operator()(long long r, int k) const {
+    return d2(tau[(long long)k * 4 * n + r]);
+  }
+};
+struct TcSrc {  // rows c*n + k, K = k': T^c[k][k']
+  const float2* tau;
+  int n;
+  __device__ __forceinline__ double2 operator()(long long r, int kp) const {
+    const int c = (int)(r / n), k = (int)(r % n);
+    const long long n4 = 4LL * n;
     if (c == 0) {
-      const float2 a = tau[(0 * n + k) * n4 + 0 * n + kp], b = tau[(1 * n + k) * n4 + 1 * n + kp];
-      x = make_float2(a.x + b.x, a.y + b.y);
-    } else {
-      const int mu = (c <= 2) ? 0 : 1;
-      const int gp = (c == 1 || c == 3) ? 2 : 3;
-      x = tau[(mu * n + k) * n4 + gp * n + kp];
+      const float2 a = tau[(long long)k * n4 + kp], b = tau[((long long)n + k) * n4 + n + kp];
+      return make_double2((double)a.x + b.x, (double)a.y + b.y);
     }
-    auto* d = Tc + (long long)c * NPL * n * ldn + k * ldn + kp;
-    store_split<BF16, NP>(d, n * ldn, 0, x.x * stc);
-    store_split<BF16, NP>(d, n * ldn, 1, x.y * stc);
+    const int mu = (c <= 2) ? 0 : 1;
+    const int gp = (c == 1 || c == 3) ? 2 : 3;
+    return d2(tau[((long long)mu * n + k) * n4 + gp * n + kp]);
   }
+};
+// sorted-triple lookup with sign; 0 on a repeated index
+__device__ __forceinline__ double2 phi_at(const double2* phi, int i, int j, int k, double w) {
+  if (i == j || j == k || i == k) return make_double2(0.0, 0.0);
+  int x = i, y = j, z = k;
+  if (x > y) { int t = x; x = y; y = t; w = -w; }
+  if (y > z) { int t = y; y = z; z = t; w = -w; }
+  if (x > y) { int t = x; x = y; y = t; w = -w; }
+  const double2 p = phi[triple_rank(x, y, z)];
+  return make_double2(p.x * w, p.y * w);
+}
+struct GSrc {  // rows a*n^2 + k*n + j, K = i: g_i g_j g_k Phi_ijk
+  const double2* phi;
+  const double* g;
+  int n;
+  __device__ __forceinline__ double2 operator()(long long r, int i) const {
+    const long long n2 = (long long)n * n;
+    const int a = (int)(r / n2);
+    const int k = (int)((r % n2) / n), j = (int)(r % n);
+    const double* ga = g + (long long)a * n;
+    return phi_at(phi, i, j, k, ga[i] * ga[j] * ga[k]);
+  }
+};
+struct SSrc {  // rows b*P2 + pair(i'<j'), K = k': g g g conj(Phi_{i'j'k'})
+  const double2* phi;
+  const double* g;
+  int n;
+  long long P2;
+  __device__ __forceinline__ double2 operator()(long long r, int kp) const {
+    const int b = (int)(r / P2);
+    int ip, jp;
+    pair_unrank(r % P2, ip, jp);
+    const double* gb = g + (long long)b * n;
+    const double2 v = phi_at(phi, ip, jp, kp, gb[ip] * gb[jp] * gb[kp]);
+    return make_double2(v.x, -v.y);
+  }
+};
+
+// eU[(a*3 + a')*n^2 + i'*n + k] = exponent of max_beta |Aa row (a'beta, i')| * max_j |G row (a, k, j)|
+__global__ void u_exponent_kernel(const float* __restrict__ nAa, const float* __restrict__ nG, int n, int nb,
+                                  int* __restrict__ eU) {
+  const long long n2 = (long long)n * n;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= 3LL * nb * n2) return;
+  const int ab = (int)(e / n2);  // a*3 + a'
+  const int a = ab / 3, ap = ab % 3;
+  const int ip = (int)((e % n2) / n), k = (int)(e % n);
+  float mA = 0.f;
+  for (int beta = 0; beta < 4; ++beta) mA = fmaxf(mA, nAa[(ap * 4 + beta) * n + ip]);
+  float mG = 0.f;
+  const float* g = nG + (long long)a * n2 + (long long)k * n;
+  for (int j = 0; j < n; ++j) mG = fmaxf(mG, g[j]);
+  eU[e] = row_exponent_d((double)mA * (double)mG * (1.0 + 1e-5));
 }
 
-// G planes [nb][NPL][n^2 rows (k,j)][ldn (i)] = s_G g_i g_j g_k Phi_ijk
-template <bool BF16, int NP>
-__global__ void split_sink_kernel(const float2* __restrict__ phi, const double* __restrict__ g, int nv, int nb,
-                                  const float* __restrict__ sc, typename tc::Piece<BF16>::T* __restrict__ G,
-                                  long long ldn) {
-  constexpr int NPL = 2 * NP;
-  const long long n = nv, n3 = n * n * n;
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= nb * n3) return;
-  const int a = (int)(e / n3);
-  const long long r = e % n3;
-  const int i = (int)(r % n), j = (int)((r / n) % n), k = (int)(r / (n * n));
-  float2 v = make_float2(0.f, 0.f);
-  if (i != j && j != k && i != k) {
-    int x = i, y = j, z = k, sgn = 1;
-    if (x > y) { int tt = x; x = y; y = tt; sgn = -sgn; }
-    if (y > z) { int tt = y; y = z; z = tt; sgn = -sgn; }
-    if (x > y) { int tt = x; x = y; y = tt; sgn = -sgn; }
-    const double* ga = g + (long long)a * nv;
-    const float w = (float)(ga[i] * ga[j] * ga[k] * sgn) * sc[SC_SG];
-    const float2 p = phi[triple_rank(x, y, z)];
-    v = make_float2(p.x * w, p.y * w);
+// Step i epilogue: split U straight from the FP64-combined accumulators into
+// the A-operand pieces of step j, U[(a,a')][plane][(i',k)][(beta,j)].
+template <bool BF16, bool FIXED, int NPC>
+struct EpiSplitU {
+  typename tc::Piece<BF16>::T* out;
+  const int* eU;
+  int n, H;
+  long long ld4;
+  __device__ __forceinline__ void operator()(int batch, int row, int col0, const double* re,
+                                             const double* im) const {
+    const long long n2 = (long long)n * n;
+    const int aa = batch >> 2, beta = batch & 3;  // aa = a*3 + a'
+    const long long ps = n2 * ld4;
+    auto* base = out + (long long)aa * (2 * NPC) * ps;
+#pragma unroll 4
+    for (int e = 0; e < 16; ++e) {
+      const int c = col0 + e;
+      if (c >= (int)n2) break;
+      const int k = c / n, j = c % n;
+      const long long ur = (long long)row * n + k;
+      const int ex = eU[(long long)aa * n2 + ur];
+      typename tc::Piece<BF16>::T pr[NPC], pi[NPC];
+      make_pieces<BF16, FIXED, NPC>(re[e], ex, H, pr);
+      make_pieces<BF16, FIXED, NPC>(im[e], ex, H, pi);
+      auto* d = base + ur * ld4 + (long long)beta * n + j;
+#pragma unroll
+      for (int q = 0; q < NPC; ++q) {
+        d[(2 * q) * ps] = pr[q];
+        d[(2 * q + 1) * ps] = pi[q];
+      }
+    }
   }
-  auto* d = G + (long long)a * NPL * n * n * ldn + ((long long)k * n + j) * ldn + i;
-  store_split<BF16, NP>(d, n * n * ldn, 0, v.x);
-  store_split<BF16, NP>(d, n * n * ldn, 1, v.y);
-}
-
-// S planes [nb][NPL][P2 rows (i'<j')][ldn (k')] = s_S g g g conj(Phi_{i'j'k'})
-template <bool BF16, int NP>
-__global__ void split_source_kernel(const float2* __restrict__ phi, const double* __restrict__ g, int nv, int nb,
-                                    const float* __restrict__ sc, typename tc::Piece<BF16>::T* __restrict__ S,
-                                    long long ldn) {
-  constexpr int NPL = 2 * NP;
-  const long long n = nv, P2 = comb2(nv);
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= nb * P2 * n) return;
-  const int b = (int)(e / (P2 * n));
-  const long long r = e % (P2 * n);
-  const long long q = r / n;
-  const int kp = (int)(r % n);
-  int ip, jp;
-  pair_unrank(q, ip, jp);
-  float2 v = make_float2(0.f, 0.f);
-  if (kp != ip && kp != jp) {
-    int x = ip, y = jp, z = kp, sgn = 1;
-    if (y > z) { int tt = y; y = z; z = tt; sgn = -sgn; }
-    if (x > y) { int tt = x; x = y; y = tt; sgn = -sgn; }
-    const double* gb = g + (long long)b * nv;
-    const float w = (float)(gb[ip] * gb[jp] * gb[kp] * sgn) * sc[SC_SS];
-    const float2 p = phi[triple_rank(x, y, z)];
-    v = make_float2(p.x * w, -p.y * w);
-  }
-  auto* d = S + (long long)b * NPL * P2 * ldn + q * ldn + kp;
-  store_split<BF16, NP>(d, P2 * ldn, 0, v.x);
-  store_split<BF16, NP>(d, P2 * ldn, 1, v.y);
-}
+};
 
 // ------------------------------------------------------------------ workspace
 struct MixedWs {
-  float* sc;
   void *Aa, *TT, *Tc, *G, *S, *U;
-  Cx<float>*V, *X;
+  int *eAa, *eTT, *eTc, *eG, *eS, *eU;
+  float *nAa, *nG;
+  Cx<double>*V, *X;
   long long ldn, ld4;
 };
 
-static MixedWs carve_mixed(Arena& ar, int np_, int nv, int nb) {
+static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nv, int nb) {
   const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv);
-  const int NPL = 2 * np_;
+  const int npa = 2 * sc.na, npb = 2 * sc.nb;
   MixedWs w;
   w.ldn = tc::pad64(n);
   w.ld4 = tc::pad64(4 * n);
-  w.sc = ar.take<float>(64);
-  w.Aa = ar.take<uint16_t>(12LL * NPL * n * w.ldn);
-  w.TT = ar.take<uint16_t>((long long)NPL * 4 * n * w.ld4);
-  w.Tc = ar.take<uint16_t>(5LL * NPL * n * w.ldn);
-  w.G = ar.take<uint16_t>((long long)nb * NPL * n2 * w.ldn);
-  w.S = ar.take<uint16_t>((long long)nb * NPL * P2 * w.ldn);
-  w.U = ar.take<uint16_t>((long long)nb * 3 * NPL * n2 * w.ld4);
-  w.V = ar.take<Cx<float>>((long long)nb * NPAIR * n3);
-  w.X = ar.take<Cx<float>>((long long)nb * NSRC * P2 * n);
+  w.Aa = ar.take<uint16_t>(12LL * npa * n * w.ldn);
+  w.TT = ar.take<uint16_t>((long long)npb * 4 * n * w.ld4);
+  w.Tc = ar.take<uint16_t>(5LL * npb * n * w.ldn);
+  w.G = ar.take<uint16_t>((long long)nb * npb * n2 * w.ldn);
+  w.S = ar.take<uint16_t>((long long)nb * npa * P2 * w.ldn);
+  w.U = ar.take<uint16_t>((long long)nb * 3 * npa * n2 * w.ld4);
+  w.eAa = ar.take<int>(12 * n);
+  w.eTT = ar.take<int>(4 * n);
+  w.eTc = ar.take<int>(5 * n);
+  w.eG = ar.take<int>(nb * n2);
+  w.eS = ar.take<int>(nb * P2);
+  w.eU = ar.take<int>(3 * nb * n2);
+  w.nAa = ar.take<float>(12 * n);
+  w.nG = ar.take<float>(nb * n2);
+  w.V = ar.take<Cx<double>>((long long)nb * NPAIR * n3);
+  w.X = ar.take<Cx<double>>((long long)nb * NSRC * P2 * n);
   return w;
 }
 
 size_t correlate_mixed_workspace(int mode, int nv, int nb) {
   Arena ar;
-  carve_mixed(ar, scheme_of(mode).np, nv, nb);
+  carve_mixed(ar, scheme_of(mode), nv, nb);
   return ar.used + 256;
 }
 
-static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
+// GEMM with the N tile chosen from N (TMEM holds 4 x NT columns).
+template <bool BF16, int NPLA, int NPLB, class Epi>
+static int gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const tc::GemmCfg& cfg,
+                int batch, const Epi& epi, cudaStream_t s) {
+  constexpr int KC = 32;
+  constexpr int ST128 = (NPLA + NPLB) > 8 ? 2 : 3;
+  if (cfg.N > 64)
+    return tc::launch_gemm<128, KC, NPLA, NPLB, ST128, BF16>(ctx, name, A, B, cfg, batch, epi, s);
+  if (cfg.N > 32) return tc::launch_gemm<64, KC, NPLA, NPLB, 2, BF16>(ctx, name, A, B, cfg, batch, epi, s);
+  return tc::launch_gemm<32, KC, NPLA, NPLB, 2, BF16>(ctx, name, A, B, cfg, batch, epi, s);
+}
 
-template <bool BF16, int NP>
-static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const float2* phs, const float2* ph0, const float2* tau,
-                        const double* g_snk, const double* g_src, int nv, int nb, const MixedWs& w,
-                        Cx<double>* Cout, long long cs_a, long long cs_b, cudaStream_t s) {
-  using P16 = typename tc::Piece<BF16>::T;
-  constexpr int NPL = 2 * NP;
+template <bool BF16, bool FIXED, int NA, int NB>
+static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs, const double2* ph0,
+                        const float2* tau, const double* g_snk, const double* g_src, int nv, int nb,
+                        const MixedWs& w, Cx<double>* Cout, long long cs_a, long long cs_b, cudaStream_t s) {
+  constexpr int NPLA = 2 * NA, NPLB = 2 * NB;
   const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv);
-  // ---- scales
-  DISTIL_CUDA(cudaMemsetAsync(w.sc, 0, 4 * sizeof(float), s));
+  using P16 = typename tc::Piece<BF16>::T;
+  // ---- split operands (one warp per row, per-row exponents)
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, AaSrc{tau, nv}, 12 * n, n, nv, sch.H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TTSrc{tau, nv}, 4 * n, 4 * n, 4 * nv, sch.H, w.TT, w.ld4, w.eTT, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TcSrc{tau, nv}, 5 * n, n, nv, sch.H, w.Tc, w.ldn, w.eTc, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, GSrc{phs, g_snk, nv}, nb * n2, n2, nv, sch.H, w.G, w.ldn, w.eG, s, w.nG)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, SSrc{ph0, g_src, nv, P2}, nb * P2, P2, nv, sch.H, w.S, w.ldn, w.eS, s)));
   {
-    Launch L(ctx, "maxabs", s);
-    unsigned* u = reinterpret_cast<unsigned*>(w.sc);
-    maxabs_kernel<float><<<64, 256, 0, s>>>((const Cx<float>*)tau, 16 * n2, u + SC_MTAU);
-    maxabs_kernel<float><<<64, 256, 0, s>>>((const Cx<float>*)phs, comb3(nv), u + SC_MPHIS);
-    maxabs_kernel<float><<<64, 256, 0, s>>>((const Cx<float>*)ph0, comb3(nv), u + SC_MPHI0);
-    prof_max_kernel<<<1, 256, 0, s>>>(g_snk, (long long)nb * nv, u + SC_MG);
-    if (g_src != g_snk) prof_max_kernel<<<1, 256, 0, s>>>(g_src, (long long)nb * nv, u + SC_MG);
-    scales_kernel<<<1, 1, 0, s>>>(w.sc, nv);
-  }
-  // ---- split operands
-  {
-    Launch L(ctx, "split_operands", s);
-    split_tau_kernel<BF16, NP><<<nblk(33 * n2), 256, 0, s>>>(tau, nv, w.sc, (P16*)w.Aa, w.ldn, (P16*)w.TT, w.ld4,
-                                                             (P16*)w.Tc);
-    split_sink_kernel<BF16, NP><<<nblk(nb * n3), 256, 0, s>>>(phs, g_snk, nv, nb, w.sc, (P16*)w.G, w.ldn);
-    split_source_kernel<BF16, NP><<<nblk(nb * P2 * n), 256, 0, s>>>(ph0, g_src, nv, nb, w.sc, (P16*)w.S, w.ldn);
+    Launch L(ctx, "u_exponent", s);
+    u_exponent_kernel<<<(unsigned)((3 * nb * n2 + 255) / 256), 256, 0, s>>>(w.nAa, w.nG, nv, nb, w.eU);
   }
   DISTIL_LAUNCH_CHECK();
-  tc::GemmCfg cfg{};
-  cfg.nprod = sch.nprod;
-  for (int i = 0; i < sch.nprod; ++i) {
-    cfg.pa[i] = sch.pa[i];
-    cfg.pb[i] = sch.pb[i];
-  }
-  cfg.err = ctx->d_error;
-  // KC / stages per scheme
-  constexpr int KC = NP == 2 ? 32 : 16;
-  constexpr int ST256 = NP == 2 ? 2 : 3;
-  constexpr int ST128 = NP == 2 ? 3 : 4;
 
-  // ---- step i: batch (a, a'beta) = nb x 12
+  tc::GemmCfg cfg{};
+  fill_products(cfg, sch);
+  cfg.err = ctx->d_error;
+
+  // ---- step i: batch (a, a'beta) = nb x 12, output split into U pieces
   {
-    Planes A{w.Aa, n, n, NPL, 12, w.ldn, n * w.ldn, NPL * n * w.ldn};
-    Planes B{w.G, n, n2, NPL, nb, w.ldn, n2 * w.ldn, NPL * n2 * w.ldn};
+    Planes A = planes_of(w.Aa, n, n, 12, NPLA, w.ldn);
+    Planes B = planes_of(w.G, n, n2, nb, NPLB, w.ldn);
     cfg.M = nv; cfg.N = (int)n2; cfg.K = nv;
-    cfg.a = tc::OpMap{1, 12, 1, 0, 0};
-    cfg.b = tc::OpMap{12, nb, 1, 0, 0};
-    EpiSplit<BF16, NP> epi;
-    epi.out = (P16*)w.U;
-    epi.b_lo = 4;
-    epi.sb_hi = (long long)NPL * n2 * w.ld4;  // (a, a') block
-    epi.sb_lo = n;                            // beta -> column offset
-    epi.plane_stride = n2 * w.ld4;
-    epi.sr = n * w.ld4;                       // i' -> rows (i', k)
-    epi.cdiv = nv; epi.cs1 = w.ld4; epi.cs0 = 1;
-    epi.N = (int)n2;
-    epi.factor = w.sc + SC_FA;
-    DISTIL_TRY((tc::launch_gemm<256, KC, NPL, ST256, BF16>(ctx, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
+    cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
+    cfg.b = tc::OpMap{12, nb, 1, 0, 0, (int)n2, w.eG};
+    EpiSplitU<BF16, FIXED, NA> epi{(P16*)w.U, w.eU, nv, sch.H, w.ld4};
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
   }
-  // ---- step j: per a' (rows b' > a'), batch a
+  // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
   for (int ap = 0; ap < 3; ++ap) {
-    Planes A{w.TT, 4 * n, 4 * n, NPL, 1, w.ld4, 4 * n * w.ld4, NPL * 4 * n * w.ld4};
-    Planes B{w.U, 4 * n, n2, NPL, 3LL * nb, w.ld4, n2 * w.ld4, NPL * n2 * w.ld4};
-    cfg.M = (3 - ap) * nv; cfg.N = (int)n2; cfg.K = 4 * nv;
-    cfg.a = tc::OpMap{1, 1, 0, 0, (ap + 1) * nv};
-    cfg.b = tc::OpMap{1, nb, 3, ap, 0};
-    EpiC64 epi;
-    epi.out = reinterpret_cast<float2*>(w.V + (long long)slotbase[ap] * n3);
+    Planes A = planes_of(w.U, 4 * n, n2, 3LL * nb, NPLA, w.ld4);
+    Planes B = planes_of(w.TT, 4 * n, 4 * n, 1, NPLB, w.ld4);
+    cfg.M = (int)n2; cfg.N = (3 - ap) * nv; cfg.K = 4 * nv;
+    cfg.a = tc::OpMap{1, nb, 3, ap, 0, (int)n2, w.eU};
+    cfg.b = tc::OpMap{1, 1, 0, 0, (ap + 1) * nv, 4 * nv, w.eTT};
+    EpiStore<double2> epi;
+    epi.out = reinterpret_cast<double2*>(w.V + (long long)slotbase[ap] * n3);
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
-    epi.sr = n2; epi.N = (int)n2;
-    epi.factor = w.sc + SC_FB;
-    DISTIL_TRY((tc::launch_gemm<256, KC, NPL, ST256, BF16>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
+    epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
   }
-  // ---- source: batch (b, c) = nb x 5
+  // ---- source: batch (b, c) = nb x 5; X[b][c][pair][k]
   {
-    Planes A{w.S, n, P2, NPL, nb, w.ldn, P2 * w.ldn, NPL * P2 * w.ldn};
-    Planes B{w.Tc, n, n, NPL, NSRC, w.ldn, n * w.ldn, NPL * n * w.ldn};
+    Planes A = planes_of(w.S, n, P2, nb, NPLA, w.ldn);
+    Planes B = planes_of(w.Tc, n, n, NSRC, NPLB, w.ldn);
     cfg.M = (int)P2; cfg.N = nv; cfg.K = nv;
-    cfg.a = tc::OpMap{NSRC, nb, 1, 0, 0};
-    cfg.b = tc::OpMap{1, NSRC, 1, 0, 0};
-    EpiC64 epi;
-    epi.out = reinterpret_cast<float2*>(w.X);
+    cfg.a = tc::OpMap{NSRC, nb, 1, 0, 0, (int)P2, w.eS};
+    cfg.b = tc::OpMap{1, NSRC, 1, 0, 0, nv, w.eTc};
+    EpiStore<double2> epi;
+    epi.out = reinterpret_cast<double2*>(w.X);
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
-    epi.sr = n; epi.N = nv;
-    epi.factor = w.sc + SC_FX;
-    if (nv > 64)
-      DISTIL_TRY((tc::launch_gemm<128, KC, NPL, ST128, BF16>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
-    else
-      DISTIL_TRY((tc::launch_gemm<64, KC, NPL, ST128, BF16>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
+    epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
   }
   // ---- dot
   {
     long long work = P2 * n;
-    unsigned gx = nblk(work);
+    unsigned gx = (unsigned)((work + 255) / 256);
     if (gx > 1024) gx = 1024;
     Launch L(ctx, "dot", s);
-    dot_kernel<float, 16><<<dim3(gx, nb), 256, 0, s>>>(w.V, w.X, nv, nb, Cout, cs_a, cs_b);
+    dot_kernel<double, 16><<<dim3(gx, nb), 256, 0, s>>>(w.V, w.X, nv, nb, Cout, cs_a, cs_b);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
@@ -298,7 +282,7 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   if (nv < 3) return DISTIL_OK;
   const Scheme sch = scheme_of(mode);
   Arena ar(ws, ws_bytes);
-  MixedWs w = carve_mixed(ar, sch.np, nv, nb);
+  MixedWs w = carve_mixed(ar, sch, nv, nb);
   if (!ar.fits()) {
     set_error("correlate: workspace too small");
     return DISTIL_ENOMEM;
@@ -308,17 +292,20 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   for (int t = 0; t < nt; ++t) {
     const double* g_snk = prof + (prof_per_t ? (long long)t * nb * nv : 0);
     for (int q = 0; q < np; ++q) {
-      const float2* phs = (const float2*)phi_snk + ((long long)t * np + q) * T3;
-      const float2* ph0 = (const float2*)phi_src + (long long)q * T3;
+      const double2* phs = (const double2*)phi_snk + ((long long)t * np + q) * T3;
+      const double2* ph0 = (const double2*)phi_src + (long long)q * T3;
       const float2* ta = (const float2*)tau + (long long)t * n4 * n4;
       Cx<double>* Cq = Cd + (long long)q * nb * nb * nt + t;
+      const long long ca = (long long)nb * nt, cb = nt;
       int st;
-      if (mode == DISTIL_MIXED_BF16X6)
-        st = run_tp_mixed<true, 3>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, (long long)nb * nt, nt, s);
+      if (mode == DISTIL_MIXED_FP16X6)
+        st = run_tp_mixed<false, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
+      else if (mode == DISTIL_MIXED_BF16X6)
+        st = run_tp_mixed<true, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
       else if (mode == DISTIL_MIXED_BF16X3)
-        st = run_tp_mixed<true, 2>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, (long long)nb * nt, nt, s);
+        st = run_tp_mixed<true, true, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
       else
-        st = run_tp_mixed<false, 2>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, (long long)nb * nt, nt, s);
+        st = run_tp_mixed<false, false, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
       if (st != DISTIL_OK) return st;
     }
   }

@@ -1,13 +1,20 @@
 // Split-precision complex GEMM on tcgen05 tensor cores.
 //
-//   D[b](m, n) = sum_k A[b](m, k) * B[b](n, k)          (complex, FP32 accumulate)
+//   D[b](m, n) = sum_k A[b](m, k) * B[b](n, k)          (complex)
 //
-// A and B arrive pre-split: each complex operand is a stack of 2*NP real
-// 16-bit planes (piece p, re/im), K contiguous, read by TMA with the swizzle
-// that matches the K-chunk (32/64/128-byte rows).  For every K step and every
-// product (pa, pb) of the split scheme four MMAs update two TMEM accumulators:
-//   D_re += A_re[pa] B_re[pb] + (-A_im[pa]) B_im[pb]   (negate-A descriptor)
-//   D_im += A_re[pa] B_im[pb] + A_im[pa] B_re[pb]
+// A and B arrive pre-split: each complex operand is a stack of 2*NA (2*NB)
+// real 16-bit planes (piece p, re/im), K contiguous, read by TMA with the
+// swizzle that matches the K chunk (32/64/128-byte rows).  For every K step
+// and every product (pa, pb, acc) of the split scheme four MMAs update the
+// accumulator pair `acc` in TMEM:
+//   D_re[acc] += A_re[pa] B_re[pb] + (-A_im[pa]) B_im[pb]   (negate-A descriptor)
+//   D_im[acc] += A_re[pa] B_im[pb] + A_im[pa] B_re[pb]
+// Two accumulator pairs exist so that the leading product of a fixed-point
+// split (integer-valued slices) sums exactly in its own FP32 accumulator,
+// whatever the tensor core's accumulation rounding; every scheme puts at
+// least one product into each pair.  The epilogue forms
+// D = D[0] + w1 * D[1] in FP64 and multiplies by 2^(eA[row] + eB[col] - shift).
+//
 // One CTA computes a 128 x NT tile: warp 0 issues TMA loads into a STAGES-deep
 // ring, warp 1 allocates TMEM and issues the MMAs, warps 2..5 read the
 // accumulators back (tcgen05.ld) and hand 16-column slices to the epilogue
@@ -20,42 +27,49 @@ namespace distil {
 namespace tc {
 
 struct OpMap {
-  int bdiv, bmod;  // operand batch coordinate = ((batch / bdiv) % bmod) * bmul + badd
+  int bdiv, bmod;   // operand batch coordinate = ((batch / bdiv) % bmod) * bmul + badd
   int bmul, badd;
-  int row_off;     // added to the tile's first row
+  int row_off;      // added to the tile's first row
+  int rows;         // rows per batch coordinate (indexing of the exponent array)
+  const int* exps;  // per-row power-of-two exponents [coord][rows] (null: 0)
   __device__ __forceinline__ int coord(int batch) const { return ((batch / bdiv) % bmod) * bmul + badd; }
+  __device__ __forceinline__ int exp_of(int c, int r) const { return exps ? exps[(long long)c * rows + r] : 0; }
 };
 
 struct GemmCfg {
   int M, N, K;
   OpMap a, b;
   int nprod;
-  int pa[6], pb[6];
+  int pa[6], pb[6], acc[6];
+  float w1;   // weight of the second accumulator pair
+  int shift;  // D *= 2^(eA + eB - shift)
   unsigned* err;
 };
 
-template <int NT, int KC, int NPL>
+template <int NT, int KC, int NPLA, int NPLB>
 struct TileGeom {
-  static constexpr int SWZ = KC * 2;                  // bytes per tile row
+  static constexpr int SWZ = KC * 2;  // bytes per tile row
   static constexpr int A_PLANE = 128 * SWZ;
   static constexpr int B_PLANE = NT * SWZ;
-  static constexpr int A_STAGE = NPL * A_PLANE;
-  static constexpr int B_STAGE = NPL * B_PLANE;
+  static constexpr int A_STAGE = NPLA * A_PLANE;
+  static constexpr int B_STAGE = NPLB * B_PLANE;
   static constexpr int STAGE = A_STAGE + B_STAGE;
 };
 
-template <int NT, int KC, int NPL, int STAGES>
+template <int NT, int KC, int NPLA, int NPLB, int STAGES>
 constexpr size_t gemm_smem_bytes() {
-  return (size_t)STAGES * TileGeom<NT, KC, NPL>::STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  return (size_t)STAGES * TileGeom<NT, KC, NPLA, NPLB>::STAGE + 1024 /*align*/ + 256 /*barriers*/;
 }
 
-template <int NT, int KC, int NPL, int STAGES, bool BF16, class Epi>
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    GemmCfg cfg, Epi epi) {
-  using G = TileGeom<NT, KC, NPL>;
-  static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "N tile");
+  using G = TileGeom<NT, KC, NPLA, NPLB>;
+  static_assert(NT % 16 == 0 && NT >= 32 && NT <= 128, "N tile");
   static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
+  // a CTA of a launch that already hit a timeout does nothing
+  if (cfg.err && *(volatile unsigned*)cfg.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -67,12 +81,10 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t* abort_flag = tslot + 1;
   uint32_t* issued_s = tslot + 2;
 
-  // a CTA of a launch that already hit a timeout does nothing
-  if (cfg.err && *(volatile unsigned*)cfg.err) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tile = blockIdx.x, m_tile = blockIdx.y, batch = blockIdx.z;
   const int nk = (cfg.K + KC - 1) / KC;
-  constexpr uint32_t TCOLS = 2 * NT;  // D_re | D_im
+  constexpr uint32_t TCOLS = 4 * NT;  // D0_re | D0_im | D1_re | D1_im
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -94,11 +106,11 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const int ca = cfg.a.coord(batch);
+  const int cb = cfg.b.coord(batch);
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------------- TMA producer
-    const int ca = cfg.a.coord(batch);
-    const int cb = cfg.b.coord(batch);
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
@@ -117,13 +129,12 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------------------------------------------------------- MMA issuer
     const uint32_t id = idesc_f16(128, NT, BF16, false);
     const uint32_t idn = idesc_f16(128, NT, BF16, true);
-    bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
+    uint32_t started = 0;  // bit a: accumulator pair a has been written
+    for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (kb / STAGES) & 1;
       if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *(volatile uint32_t*)abort_flag) {
         *(volatile uint32_t*)abort_flag = 1;
-        ok = false;
         break;
       }
       tc_fence_after();
@@ -138,11 +149,14 @@ __global__ void __launch_bounds__(192, 1)
           const uint32_t bi = br + G::B_PLANE;
           const uint64_t dar = smem_desc(ar, G::SWZ), dai = smem_desc(ai, G::SWZ);
           const uint64_t dbr = smem_desc(br, G::SWZ), dbi = smem_desc(bi, G::SWZ);
-          const uint32_t acc = (kb > 0 || ks > 0 || p > 0) ? 1u : 0u;
-          mma_f16(tmem, dar, dbr, id, acc);
-          mma_f16(tmem, dai, dbi, idn, 1u);
-          mma_f16(tmem + NT, dar, dbi, id, acc);
-          mma_f16(tmem + NT, dai, dbr, id, 1u);
+          const int a = cfg.acc[p];
+          const uint32_t d = tmem + (uint32_t)(a * 2 * NT);
+          const uint32_t accum = (started >> a) & 1u;
+          mma_f16(d, dar, dbr, id, accum);
+          mma_f16(d, dai, dbi, idn, 1u);
+          mma_f16(d + NT, dar, dbi, id, accum);
+          mma_f16(d + NT, dai, dbr, id, 1u);
+          started |= 1u << a;
         }
       }
       mma_commit(&empty[s]);
@@ -157,14 +171,28 @@ __global__ void __launch_bounds__(192, 1)
     if (ok) {
       const int row = m_tile * 128 + q * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+      const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
       for (int c = 0; c < NT / 16; ++c) {
-        uint32_t re[16], im[16];
-        tmem_ld16(tl + c * 16, re);
-        tmem_ld16(tl + NT + c * 16, im);
+        uint32_t r0[16], i0[16], r1[16], i1[16];
+        tmem_ld16(tl + c * 16, r0);
+        tmem_ld16(tl + NT + c * 16, i0);
+        tmem_ld16(tl + 2 * NT + c * 16, r1);
+        tmem_ld16(tl + 3 * NT + c * 16, i1);
         tmem_wait_ld();
-        if (row < cfg.M) epi(batch, row, n_tile * NT + c * 16, reinterpret_cast<const float*>(re),
-                             reinterpret_cast<const float*>(im));
+        const int col0 = n_tile * NT + c * 16;
+        if (row < cfg.M) {
+          double re[16], im[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = col0 + e;
+            const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
+            const double f = ldexp(1.0, ea + eb - cfg.shift);
+            re[e] = fma((double)cfg.w1, (double)__uint_as_float(r1[e]), (double)__uint_as_float(r0[e])) * f;
+            im[e] = fma((double)cfg.w1, (double)__uint_as_float(i1[e]), (double)__uint_as_float(i0[e])) * f;
+          }
+          epi(batch, row, col0, re, im);
+        }
       }
     }
     tc_fence_before();
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(192, 1)
   if (threadIdx.x == 0 && *(volatile uint32_t*)abort_flag) {
     // drain: wait (bounded) for the last load of every stage, so no copy
     // lands in shared memory after the CTA has exited
-    const int issued = *(volatile uint32_t*)issued_s;
+    const int issued = (int)*(volatile uint32_t*)issued_s;
     for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
       if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
     }

@@ -22,7 +22,7 @@ inline long long pad64(long long k) { return (k + 63) / 64 * 64; }
 
 int encode_planes(CUtensorMap* map, const Planes& t, int box_rows, int kc, bool bf16);
 
-template <int NT, int KC, int NPL, int STAGES, bool BF16, class Epi>
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
 int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg,
                 int batch, const Epi& epi, cudaStream_t s) {
   if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
@@ -33,8 +33,9 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
   CUtensorMap ma, mb;
   DISTIL_TRY(encode_planes(&ma, A, 128, KC, BF16));
   DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
-  constexpr size_t smem = gemm_smem_bytes<NT, KC, NPL, STAGES>();
-  auto kern = tc_gemm_kernel<NT, KC, NPL, STAGES, BF16, Epi>;
+  constexpr size_t smem = gemm_smem_bytes<NT, KC, NPLA, NPLB, STAGES>();
+  static_assert(smem <= 232448, "shared memory");
+  auto kern = tc_gemm_kernel<NT, KC, NPLA, NPLB, STAGES, BF16, Epi>;
   static bool attr = false;
   if (!attr) {
     DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -23,9 +23,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdistil.so")
 
-FP64, FP32, MIXED_BF16X6, MIXED_BF16X3, MIXED_FP16X3 = 0, 1, 2, 3, 4
+FP64, FP32, MIXED_BF16X6, MIXED_BF16X3, MIXED_FP16X3, MIXED_FP16X6 = 0, 1, 2, 3, 4, 5
 MODE_NAMES = {FP64: "fp64", FP32: "fp32", MIXED_BF16X6: "bf16x6", MIXED_BF16X3: "bf16x3",
-              MIXED_FP16X3: "fp16x3"}
+              MIXED_FP16X3: "fp16x3", MIXED_FP16X6: "fp16x6"}
 MODES = {v: k for k, v in MODE_NAMES.items()}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP"}
 

@@ -36,3 +36,16 @@ def phi_error(got, ref) -> float:
     ref = np.asarray(ref, dtype=np.complex128)
     scale = np.maximum(np.abs(ref).max(axis=-1, keepdims=True), 1e-300)
     return float((np.abs(got - ref) / scale).max())
+
+
+def c_scaled_errors(got, ref) -> np.ndarray:
+    """Per-entry error relative to the scale of its matrix C(p, t):
+    |dC_ab(t)| / max_a'b' |C_a'b'(t)|  ->  [np][nb][nb][nt]."""
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    scale = np.maximum(np.abs(ref).max(axis=(1, 2), keepdims=True), 1e-300)
+    return np.abs(got - ref) / scale
+
+
+def max_c_scaled_error(got, ref) -> float:
+    return float(c_scaled_errors(got, ref).max())
