@@ -205,7 +205,7 @@ def run_ours(args):
     from paper_2609_37723_b300 import distil
     mode = args.mode
     if mode == "auto":
-        mode = next((m for m in ("fp16x3", "bf16x6") if distil.mode_available(m)), "fp32")
+        mode = next((m for m in ("fp16x6", "bf16x6") if distil.mode_available(m)), "fp32")
     c128 = mode == "fp64"
     cdt = np.complex128 if c128 else np.complex64
     v_h = np.ascontiguousarray(v_h.astype(cdt))
@@ -223,7 +223,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     T3 = p.T3
-    tdt = torch.complex128 if c128 else torch.complex64
+    tdt = torch.complex64 if mode == "fp32" else torch.complex128   # tensor-core modes keep c128 elementals
     phi = torch.empty((p.nt, p.np_, T3), dtype=tdt, device=dev)
     C = torch.empty((p.np_, p.nb, p.nb, p.nt), dtype=torch.complex128, device=dev)
     lam = torch.empty((p.np_, p.nt, p.nb), dtype=torch.complex128, device=dev)
@@ -303,8 +303,7 @@ def run_ours(args):
     if rank == 0:
         flops = algorithmic_flops(p)
         pk = peaks()
-        gemm_names = [k for k in kstats if k.startswith(("tc_gemm", "simt_gemm", "elementals"))]
-        dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+            dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
         roof = roofline(dom, kstats, p, mode, pk, args.steps)
         launches = sum(l for l, _ in kstats.values())
         parity = parity_slice(p, v_h, tau_h, C.cpu().numpy(), mode) if not args.no_parity else None
@@ -334,22 +333,33 @@ def run_ours(args):
     return out
 
 
+def kernel_cmacs(name, p):
+    """Complex MACs one step asks of a kernel family (the per-unit counts of
+    the contraction each family runs, times the units per step)."""
+    n, nb, tp = p.nv, p.nb, p.nt * p.np_
+    P2 = n * (n - 1) // 2
+    table = {
+        "tc_gemm_step_i": (12.0 * nb * n ** 4 * tp, "12 N_B N_v^4 per (t,p): i contraction, 12 spin blocks, all (k,j)"),
+        "tc_gemm_step_j": (24.0 * nb * n ** 4 * tp, "24 N_B N_v^4 per (t,p): j contraction, 6 spin pairs, K = 4 N_v"),
+        "tc_gemm_source": (5.0 * nb * P2 * n * n * tp, "5 N_B C(N_v,2) N_v^2 per (t,p): k' contraction"),
+        "tc_gemm_elementals": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p): useful i<j<k MACs"),
+        "elementals_simt_f32": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p)"),
+        "elementals_simt_f64": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p)"),
+        "simt_gemm_f32": ((36.0 * nb * n ** 4 + 5.0 * nb * P2 * n * n) * tp, "38.5 N_B N_v^4 per (t,p)"),
+        "simt_gemm_f64": ((36.0 * nb * n ** 4 + 5.0 * nb * P2 * n * n) * tp, "38.5 N_B N_v^4 per (t,p)"),
+    }
+    return table.get(name)
+
+
 def roofline(dom, kstats, p, mode, pk, steps):
     """Roofline of the dominant kernel family over the timed region."""
     if dom is None:
         return None
     launches, ms = kstats[dom]
-    n = p.nv
-    tp = p.nt * p.np_
-    P2 = n * (n - 1) // 2
-    if dom.startswith("elementals"):
-        cm = 3.0 * p.V3 * p.T3 * tp          # useful complex MACs (i<j<k)
-        what = "elementals: 3 V3 T3 complex MACs per (t,p)"
-    elif "gemm" in dom:
-        cm = (12 + 24) * p.nb * n ** 4 * tp + 5.0 * p.nb * P2 * n * n * tp
-        what = "mode contractions: (36 N_B n^4 + 2.5 N_B n^4) complex MACs per (t,p)"
-    else:
+    ent = kernel_cmacs(dom, p)
+    if ent is None:
         return {"kernel": dom, "note": "no flop model"}
+    cm, what = ent
     flop = 8.0 * cm * steps
     achieved = flop / (ms / 1e3) / 1e12
     if mode in ("fp64", "fp32"):
@@ -357,11 +367,12 @@ def roofline(dom, kstats, p, mode, pk, steps):
         bound = "alu"
         note = "CUDA-core path; peak FP32/FP64 SIMT not in MEASURED_PEAKS"
     else:
-        prod = {"bf16x6": 6, "bf16x3": 3, "fp16x3": 3}[mode]
+        prod = {"bf16x6": 6, "bf16x3": 3, "fp16x3": 3, "fp16x6": 6}[mode]
         peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
         achieved *= prod   # issued 16-bit tensor flops
         bound = "tensor"
-        note = f"issued {prod} split products per complex MAC vs measured bf16 sustained peak"
+        note = (f"achieved = 8 x {prod} split products x complex MACs / event time: tensor flops the "
+                f"kernel must issue; peak = measured bf16 sustained (fp16 runs at the same rate)")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if peak else None, "traffic": None, "per_unit": what,
             "launches": launches, "ms": ms, "note": note}

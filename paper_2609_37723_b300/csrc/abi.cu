@@ -107,8 +107,7 @@ int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv, con
     set_error("distil_elementals: workspace %zu < %zu bytes", ws_bytes, need);
     return DISTIL_ENOMEM;
   }
-  return elementals_mixed(ctx, (const Cx<float>*)v, L, nt, nv, mom, np, mode, (Cx<float>*)phi, workspace,
-                          ws_bytes, s);
+  return elementals_mixed(ctx, (const Cx<float>*)v, L, nt, nv, mom, np, mode, phi, workspace, ws_bytes, s);
 }
 
 int distil_correlate_workspace(int nt, int nv, int np, int nb, int mode, size_t* bytes) {

@@ -7,7 +7,7 @@ namespace distil {
 int mixed_mode_built(int mode);
 size_t elementals_mixed_workspace(int L, int nt, int nv, int np, int mode);
 int elementals_mixed(distil_ctx* ctx, const Cx<float>* v, int L, int nt, int nv, const int32_t* mom, int np,
-                     int mode, Cx<float>* phi, void* ws, size_t ws_bytes, cudaStream_t s);
+                     int mode, void* phi, void* ws, size_t ws_bytes, cudaStream_t s);
 
 size_t correlate_mixed_workspace(int mode, int nv, int nb);
 int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* phi_src, const void* tau, int nt,

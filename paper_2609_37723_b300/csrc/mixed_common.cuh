@@ -195,6 +195,7 @@ struct EpiStore {
   long long sr;
   ColMap cm;
   int N;
+  __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
   __device__ __forceinline__ void operator()(int batch, int row, int col0, const double* re, const double* im) const {
     OUT* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
 #pragma unroll

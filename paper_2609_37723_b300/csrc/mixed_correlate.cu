@@ -123,6 +123,7 @@ struct EpiSplitU {
   const int* eU;
   int n, H;
   long long ld4;
+  __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
   __device__ __forceinline__ void operator()(int batch, int row, int col0, const double* re,
                                              const double* im) const {
     const long long n2 = (long long)n * n;

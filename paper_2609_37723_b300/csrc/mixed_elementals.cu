@@ -1,0 +1,255 @@
+// Mixed-precision nucleon elementals on tcgen05 tensor cores.
+//
+//   Phi[t][q]_ijk = sum_(x,a) E_(i,q)(x,a) W_(j,k)(x,a),
+//   E_(i,q)(x,a) = exp(-i p_q.x) v_i^a(x),   W_(j,k) = v_j x v_k (colour cross product)
+//
+// per timeslice as one complex GEMM with M = pairs j<k (ordered by j, then
+// k), N = (i, q) rows and K = (site, colour).  K is cut into chunks of
+// EL_KC values: per chunk the operands are formed in FP64 from the
+// eigenvectors and split into 16-bit pieces with per-(row, chunk) exponents,
+// the tensor cores accumulate the chunk in TMEM (the leading fixed-point
+// slice exactly), and the epilogue adds the chunk into an FP64 accumulator
+// Phi_acc[pair][(i,q)].  Tiles whose every i is >= every j are skipped.  A
+// final pass packs i<j<k into Phi[t][q][rank].
+#include <math.h>
+
+#include "elementals.cuh"
+#include "mixed.cuh"
+#include "mixed_common.cuh"
+
+namespace distil {
+
+using tc::Planes;
+
+constexpr int EL_KC = 4096;  // K values per accumulation chunk
+constexpr int EL_H = 10;     // leading-slice width of the elemental operands (FP16)
+
+// pairs in j-major order: q -> (j, k), first index j, then k = j+1..n-1
+__host__ __device__ __forceinline__ long long jmajor_first(long long j, long long n) { return j * (2 * n - j - 1) / 2; }
+__global__ void pair_table_kernel(int n, int2* pairs) {
+  const long long P2 = comb2(n);
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= P2) return;
+  const double b = 2.0 * n - 1.0;
+  long long j = (long long)floor((b - sqrt(b * b - 8.0 * (double)q)) * 0.5);
+  if (j < 0) j = 0;
+  while (j > 0 && jmajor_first(j, n) > q) --j;
+  while (jmajor_first(j + 1, n) <= q) ++j;
+  pairs[q] = make_int2((int)j, (int)(q - jmajor_first(j, n) + j + 1));
+}
+
+__global__ void phase_table_kernel(int L, double2* tab) {
+  const int m = threadIdx.x + blockIdx.x * blockDim.x;
+  if (m >= L) return;
+  double s, c;
+  sincospi(2.0 * (double)m / (double)L, &s, &c);
+  tab[m] = make_double2(c, -s);  // exp(-2 pi i m / L)
+}
+
+struct MomArgs {
+  int np, L;
+  int mom[EL_MAX_MOM][3];
+};
+
+struct WSrc {  // rows q (pairs), K = (x, a) from K0
+  const float2* v;  // v[t] = [n][V3][3]
+  const int2* pairs;
+  long long V3;
+  long long K0;
+  __device__ __forceinline__ double2 operator()(long long q, int kk) const {
+    const long long K = K0 + kk;
+    const long long x = K / 3;
+    const int a = (int)(K % 3), b = (a + 1) % 3, c = (a + 2) % 3;
+    const int2 jk = pairs[q];
+    const float2* vj = v + ((long long)jk.x * V3 + x) * 3;
+    const float2* vk = v + ((long long)jk.y * V3 + x) * 3;
+    const double2 jb = make_double2(vj[b].x, vj[b].y), jc = make_double2(vj[c].x, vj[c].y);
+    const double2 kb = make_double2(vk[b].x, vk[b].y), kc = make_double2(vk[c].x, vk[c].y);
+    // w^a = v_j^b v_k^c - v_j^c v_k^b
+    return make_double2(jb.x * kc.x - jb.y * kc.y - (jc.x * kb.x - jc.y * kb.y),
+                        jb.x * kc.y + jb.y * kc.x - (jc.x * kb.y + jc.y * kb.x));
+  }
+};
+
+struct ESrc {  // rows i*np + q, K = (x, a) from K0
+  const float2* v;
+  const double2* tab;
+  MomArgs m;
+  long long V3;
+  long long K0;
+  __device__ __forceinline__ double2 operator()(long long r, int kk) const {
+    const long long K = K0 + kk;
+    const long long x = K / 3;
+    const int a = (int)(K % 3);
+    const int i = (int)(r / m.np), q = (int)(r % m.np);
+    const int L = m.L;
+    const int xs = (int)(x % L), ys = (int)((x / L) % L), zs = (int)(x / ((long long)L * L));
+    const int ph = (m.mom[q][0] * xs + m.mom[q][1] * ys + m.mom[q][2] * zs) % L;
+    const double2 e = tab[ph];
+    const float2 u = v[((long long)i * V3 + x) * 3 + a];
+    return make_double2(e.x * u.x - e.y * u.y, e.x * u.y + e.y * u.x);
+  }
+};
+
+// Phi_acc[q][r] (+)= D for the pair rows q and (i, q') columns r; the first
+// chunk stores.  Tiles with min i >= max j hold no kept output.
+struct EpiPhiAcc {
+  double2* acc;
+  const int2* pairs;
+  long long P2;
+  int N, np, first, nt;  // nt: N tile width of the launch
+  __device__ __forceinline__ bool skip_tile(int m_tile, int n_tile, int) const {
+    long long qlast = (long long)m_tile * 128 + 127;
+    if (qlast >= P2) qlast = P2 - 1;
+    const int jmax = pairs[qlast].x;       // j never decreases along the pair order
+    const int imin = (n_tile * nt) / np;   // rows are i * np + q
+    return imin >= jmax;
+  }
+  __device__ __forceinline__ void operator()(int, int row, int col0, const double* re, const double* im) const {
+    double2* dst = acc + (long long)row * N + col0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if (col0 + e >= N) break;
+      double2 v = make_double2(re[e], im[e]);
+      if (!first) {
+        const double2 o = dst[e];
+        v.x += o.x;
+        v.y += o.y;
+      }
+      dst[e] = v;
+    }
+  }
+};
+
+// Phi[q][rank(i,j,k)] = Phi_acc[pair(j,k)][i*np + q]
+__global__ void pack_phi_kernel(const double2* __restrict__ acc, int n, int np, double2* __restrict__ phi) {
+  const long long T3 = comb3(n);
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= T3 * np) return;
+  const int q = (int)(e / T3);
+  const long long r = e % T3;
+  // unrank r -> (i, j, k): k from C(k,3) <= r, then j from C(j,2) <= r - C(k,3)
+  int k = (int)cbrt(6.0 * (double)r) + 1;
+  while (comb3(k) > r) --k;
+  while (comb3(k + 1) <= r) ++k;
+  const long long r2 = r - comb3(k);
+  int j, i;
+  pair_unrank(r2, i, j);  // r2 = C(j,2) + i
+  const long long qp = jmajor_first(j, n) + (k - j - 1);
+  phi[e] = acc[qp * (long long)(n * np) + (long long)i * np + q];
+}
+
+struct ElemWs {
+  int2* pairs;
+  double2* tab;
+  void *W, *E;
+  int *eW, *eE;
+  double2* acc;
+  long long ldk;
+};
+
+static ElemWs carve_elem(Arena& ar, const Scheme& sc, int L, int nv, int np) {
+  const long long P2 = comb2(nv), R = (long long)nv * np;
+  ElemWs w;
+  w.ldk = tc::pad64(EL_KC);
+  w.pairs = ar.take<int2>(P2 > 0 ? P2 : 1);
+  w.tab = ar.take<double2>(L);
+  w.W = ar.take<uint16_t>(2LL * sc.na * P2 * w.ldk);
+  w.E = ar.take<uint16_t>(2LL * sc.nb * R * w.ldk);
+  w.eW = ar.take<int>(P2 > 0 ? P2 : 1);
+  w.eE = ar.take<int>(R);
+  w.acc = ar.take<double2>(P2 * R);
+  return w;
+}
+
+size_t elementals_mixed_workspace(int L, int nt, int nv, int np, int mode) {
+  (void)nt;
+  Arena ar;
+  carve_elem(ar, scheme_of(mode), L, nv, np);
+  return ar.used + 256;
+}
+
+template <bool BF16, bool FIXED, int NA, int NB>
+static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, int L, int nv, const MomArgs& mom,
+                  double2* phi_t, const ElemWs& w, cudaStream_t s) {
+  constexpr int NPLA = 2 * NA, NPLB = 2 * NB;
+  const long long V3 = (long long)L * L * L, Ktot = 3 * V3, P2 = comb2(nv), R = (long long)nv * mom.np;
+  tc::GemmCfg cfg{};
+  fill_products(cfg, sch);
+  cfg.shift = 2 * H;
+  cfg.err = ctx->d_error;
+  for (long long K0 = 0; K0 < Ktot; K0 += EL_KC) {
+    const int Kc = (int)((Ktot - K0) < EL_KC ? (Ktot - K0) : EL_KC);
+    DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, WSrc{vt, w.pairs, V3, K0}, P2, P2, Kc, H, w.W, w.ldk, w.eW, s)));
+    DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, ESrc{vt, w.tab, mom, V3, K0}, R, R, Kc, H, w.E, w.ldk, w.eE, s)));
+    Planes A = planes_of(w.W, Kc, P2, 1, NPLA, w.ldk);
+    Planes B = planes_of(w.E, Kc, R, 1, NPLB, w.ldk);
+    cfg.M = (int)P2; cfg.N = (int)R; cfg.K = Kc;
+    cfg.a = tc::OpMap{1, 1, 0, 0, 0, (int)P2, w.eW};
+    cfg.b = tc::OpMap{1, 1, 0, 0, 0, (int)R, w.eE};
+    EpiPhiAcc epi{w.acc, w.pairs, P2, (int)R, mom.np, K0 == 0 ? 1 : 0, 128};
+    constexpr int ST = (NPLA + NPLB) > 8 ? 2 : 3;
+    int st;
+    if (R > 64) {
+      st = tc::launch_gemm<128, 32, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+    } else if (R > 32) {
+      epi.nt = 64;
+      st = tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+    } else {
+      epi.nt = 32;
+      st = tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+    }
+    DISTIL_TRY(st);
+  }
+  {
+    const long long work = comb3(nv) * mom.np;
+    Launch Lz(ctx, "pack_phi", s);
+    pack_phi_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(w.acc, nv, mom.np, phi_t);
+  }
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
+int elementals_mixed(distil_ctx* ctx, const Cx<float>* v, int L, int nt, int nv, const int32_t* mom, int np,
+                     int mode, void* phi, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (comb3(nv) == 0) return DISTIL_OK;
+  const Scheme sch = scheme_of(mode);
+  Arena ar(ws, ws_bytes);
+  ElemWs w = carve_elem(ar, sch, L, nv, np);
+  if (!ar.fits()) {
+    set_error("distil_elementals: workspace too small");
+    return DISTIL_ENOMEM;
+  }
+  MomArgs m;
+  m.np = np;
+  m.L = L;
+  for (int q = 0; q < np; ++q)
+    for (int d = 0; d < 3; ++d) m.mom[q][d] = ((mom[3 * q + d] % L) + L) % L;
+  {
+    Launch Lz(ctx, "elementals_setup", s);
+    pair_table_kernel<<<(unsigned)((comb2(nv) + 255) / 256), 256, 0, s>>>(nv, w.pairs);
+    phase_table_kernel<<<(L + 255) / 256, 256, 0, s>>>(L, w.tab);
+  }
+  DISTIL_LAUNCH_CHECK();
+  const long long V3 = (long long)L * L * L, T3 = comb3(nv);
+  // the elementals keep their own leading-slice width (long K); floating
+  // pieces keep the scheme's
+  const int H = sch.fixed ? (sch.bf16 ? sch.H : EL_H) : sch.H;
+  for (int t = 0; t < nt; ++t) {
+    const float2* vt = reinterpret_cast<const float2*>(v) + (long long)t * nv * V3 * 3;
+    double2* pt = reinterpret_cast<double2*>(phi) + (long long)t * np * T3;
+    int st;
+    if (mode == DISTIL_MIXED_FP16X6)
+      st = elem_t<false, true, 3, 4>(ctx, sch, H, vt, L, nv, m, pt, w, s);
+    else if (mode == DISTIL_MIXED_BF16X6)
+      st = elem_t<true, true, 3, 4>(ctx, sch, H, vt, L, nv, m, pt, w, s);
+    else if (mode == DISTIL_MIXED_BF16X3)
+      st = elem_t<true, true, 2, 2>(ctx, sch, H, vt, L, nv, m, pt, w, s);
+    else
+      st = elem_t<false, false, 2, 2>(ctx, sch, H, vt, L, nv, m, pt, w, s);
+    if (st != DISTIL_OK) return st;
+  }
+  return DISTIL_OK;
+}
+
+}  // namespace distil

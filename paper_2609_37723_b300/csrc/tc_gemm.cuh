@@ -68,8 +68,10 @@ __global__ void __launch_bounds__(192, 1)
   using G = TileGeom<NT, KC, NPLA, NPLB>;
   static_assert(NT % 16 == 0 && NT >= 32 && NT <= 128, "N tile");
   static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
-  // a CTA of a launch that already hit a timeout does nothing
+  // a CTA of a launch that already hit a timeout does nothing; the epilogue
+  // may declare a tile empty (no output it keeps) before anything is set up
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
+  if (epi.skip_tile(blockIdx.y, blockIdx.x, blockIdx.z)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;

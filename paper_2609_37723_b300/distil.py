@@ -158,8 +158,9 @@ def elementals(v, L: int, mom, mode="fp64", out=None, workspace=None, stream=Non
     np_ = mom_np.shape[0]
     cdt = torch.complex128 if mode == FP64 else torch.complex64
     assert v.dtype == cdt, f"v must be {cdt} for mode {MODE_NAMES[mode]}"
+    odt = torch.complex64 if mode == FP32 else torch.complex128   # tensor-core modes keep c128 elementals
     if out is None:
-        out = torch.empty((nt, np_, n_triples(nv)), dtype=cdt, device=v.device)
+        out = torch.empty((nt, np_, n_triples(nv)), dtype=odt, device=v.device)
     ws_bytes = elementals_workspace(L, nt, nv, np_, mode)
     if workspace is None:
         workspace = _workspace(ws_bytes, v.device)

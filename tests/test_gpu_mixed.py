@@ -75,3 +75,43 @@ def test_correlate_mixed_odd(cuda_lib, mode, L, nt, nv, nb):
     e = max_c_scaled_error(got, ref)
     print(f"correlate {mode} L={L} nv={nv}: scaled {e:.2e} strict {max_c_error(got, ref):.2e}")
     assert e < TOL_C[mode]
+
+
+# ------------------------------------------------------------------ elementals
+
+TOL_PHI = {"fp16x6": 3e-7, "bf16x6": 3e-6, "bf16x3": 1e-3, "fp16x3": 1e-4}
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("L,nt,nv,mom", [
+    (8, 2, 16, [(0, 0, 0), (1, 0, 0)]),             # workload-1 shape, one K chunk
+    (12, 1, 20, [(0, 0, 0), (1, 1, 0), (0, -1, 2)]),  # two K chunks (3 V3 = 5184)
+    (3, 2, 7, [(1, 0, 0)]),                          # tiny, ragged everywhere
+])
+def test_elementals_mixed(cuda_lib, mode, L, nt, nv, mom):
+    from paper_2609_37723_b300 import distil
+    from parity import phi_error
+    p = synth.small(L, nt, nv, mom=mom, seed_cfg=L + nv, dtype=np.complex64)
+    v = p.all_eigvecs()
+    ref = orc.elementals(v, p.L, p.mom)
+    got = distil.elementals(T(v), p.L, p.mom, mode).cpu().numpy()
+    assert got.dtype == np.complex128 and got.shape == ref.shape
+    e = phi_error(got, ref)
+    print(f"elementals {mode} L={L} nv={nv}: {e:.2e}")
+    assert e < TOL_PHI[mode]
+
+
+def test_chain_fp16x6_c1(cuda_lib):
+    """Workload 1 end to end on the tensor cores: elementals, correlation
+    matrix and GEVP against the FP64 oracle on the same complex64 inputs."""
+    from paper_2609_37723_b300 import distil
+    p = synth.config(1)
+    v = p.all_eigvecs().astype(np.complex64)
+    tau = p.all_perambulators().astype(np.complex64)
+    ref_phi = orc.elementals(v, p.L, p.mom)
+    ref_C = orc.correlator(ref_phi, ref_phi[0], tau, p.prof)
+    ph = distil.elementals(T(v), p.L, p.mom, "fp16x6")
+    C = distil.correlate(ph, ph[0].contiguous(), T(tau), T(p.prof), "fp16x6")
+    e = max_c_scaled_error(C.cpu().numpy(), ref_C)
+    print(f"chain fp16x6 c1: scaled {e:.2e} strict {max_c_error(C.cpu().numpy(), ref_C):.2e}")
+    assert e < 1e-6
