@@ -115,7 +115,7 @@ int distil_correlate_workspace(int nt, int nv, int np, int nb, int mode, size_t*
   DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
   DISTIL_CHECK_ARG(valid_mode(mode), "bad mode %d", mode);
   DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1 && nb >= 1 && nb <= 16, "bad sizes");
-  if (is_mixed(mode)) *bytes = correlate_mixed_workspace(mode, nv, nb);
+  if (is_mixed(mode)) *bytes = correlate_mixed_workspace(mode, nt, nv, np, nb);
   else *bytes = correlate_plain_workspace(mode == DISTIL_FP64, nv, nb);
   return DISTIL_OK;
 }

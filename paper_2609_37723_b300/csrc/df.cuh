@@ -1,0 +1,78 @@
+// Double-float arithmetic: a value held as an unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significant bits), built from the error-free
+// transformations TwoSum (Knuth) and TwoProduct (with a fused multiply-add).
+// B300 runs FP64 at a small fraction of its FP32 rate, so the mixed path
+// keeps its high-precision intermediates in this form and does its
+// element-wise work in FP32 instructions.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace distil {
+
+struct DF {
+  float hi, lo;
+};
+struct CDF {  // complex double-float, 16 bytes like complex128
+  DF re, im;
+};
+
+__device__ __forceinline__ DF df_make(float hi, float lo) { DF r; r.hi = hi; r.lo = lo; return r; }
+
+// s + e = a + b exactly
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df_make(s, e);
+}
+// s + e = a + b exactly when |a| >= |b|
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// p + e = a * b exactly
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return df_make(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  const DF t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return df_make(-a.hi, -a.lo); }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  DF p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  DF p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+// exact scaling by a power of two
+__device__ __forceinline__ DF df_ldexp(DF a, int e) { return df_make(ldexpf(a.hi, e), ldexpf(a.lo, e)); }
+__device__ __forceinline__ DF df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return df_make(hi, __double2float_rn(x - (double)hi));
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ CDF cdf_make(DF re, DF im) { CDF c; c.re = re; c.im = im; return c; }
+__device__ __forceinline__ CDF cdf_add(CDF a, CDF b) { return cdf_make(df_add(a.re, b.re), df_add(a.im, b.im)); }
+__device__ __forceinline__ CDF cdf_sub(CDF a, CDF b) { return cdf_make(df_sub(a.re, b.re), df_sub(a.im, b.im)); }
+__device__ __forceinline__ CDF cdf_mul(CDF a, CDF b) {
+  return cdf_make(df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re)));
+}
+__device__ __forceinline__ CDF cdf_scale(CDF a, DF s) { return cdf_make(df_mul(a.re, s), df_mul(a.im, s)); }
+__device__ __forceinline__ CDF cdf_conj(CDF a) { return cdf_make(a.re, df_neg(a.im)); }
+__device__ __forceinline__ CDF cdf_ldexp(CDF a, int e) { return cdf_make(df_ldexp(a.re, e), df_ldexp(a.im, e)); }
+__device__ __forceinline__ CDF cdf_zero() { return cdf_make(df_make(0.f, 0.f), df_make(0.f, 0.f)); }
+
+}  // namespace distil

@@ -9,7 +9,7 @@ size_t elementals_mixed_workspace(int L, int nt, int nv, int np, int mode);
 int elementals_mixed(distil_ctx* ctx, const Cx<float>* v, int L, int nt, int nv, const int32_t* mom, int np,
                      int mode, void* phi, void* ws, size_t ws_bytes, cudaStream_t s);
 
-size_t correlate_mixed_workspace(int mode, int nv, int nb);
+size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb);
 int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* phi_src, const void* tau, int nt,
                     int nv, int np, const double* prof, int nb, int prof_per_t, void* C, void* ws,
                     size_t ws_bytes, cudaStream_t s);

@@ -1,6 +1,8 @@
 // Pieces shared by the mixed-precision (split 16-bit, tensor-core) paths:
 // split schemes, per-row power-of-two exponents, the row-splitting kernel
-// and the GEMM epilogues.
+// and the GEMM epilogues.  Element-wise work runs in FP32 instructions on
+// double-float values (df.cuh); FP64 is used only for a handful of values
+// per block.
 //
 // Split schemes.  A row of an operand with max |x| < 2^e is represented as
 //  * fixed-point slices: t = x 2^(H-e) = hi + 2^-W mid + 2^-2W lo with hi,
@@ -10,16 +12,15 @@
 //    the tensor core accumulates exactly in FP32, whatever its rounding, as
 //    long as the partial sums stay below 2^24 (guaranteed for
 //    K <= 2^(23 - 2H); for rows of random sign the partial sums grow like
-//    sqrt(K) and the bound is met up to K ~ 2^(47 - 4H + 2 log2(4))).  The
-//    cross terms go to a second accumulator weighted 2^-W; it holds values
-//    about 2^-W |mid/hi| of the result, so its inexact rounding stays far
-//    below the target.  A pieces: hi, mid, lo 2^-W.  B pieces: hi, mid,
-//    mid 2^-W, lo 2^-W (hi*lo, mid*mid, lo*hi all carry 2^-2W).  Dropped
-//    terms (mid*lo, lo*mid, lo*lo) are of relative size 2^-3W |mid lo| /
-//    |hi|^2: about 2^-33 * 2^(22 - 2H + 4) for FP16, so H trades the
-//    dropped-term error against the exactness range: H = 9 for the short
-//    (K <= 4 N_v) mode contractions, H = 8 for the long (K = 3 V3)
-//    elemental contraction.
+//    sqrt(K) |hi|^2 and stay far below that for the K used here).  The cross
+//    terms go to a second accumulator weighted 2^-W; it holds values of about
+//    2^-W |mid/hi| of the result, so its inexact rounding stays far below the
+//    target.  A pieces: hi, mid, lo 2^-W.  B pieces: hi, mid, mid 2^-W,
+//    lo 2^-W (hi*lo, mid*mid, lo*hi all carry 2^-2W).  Dropped terms
+//    (mid*lo, lo*mid, lo*lo) are of relative size 2^-3W |mid lo| / |hi|^2,
+//    so H trades the dropped-term error against the exactness range: H = 9
+//    for the short (K <= 4 N_v) mode contractions, H = 10 with K chunks of
+//    4096 for the long (K = 3 V3) elemental contraction.
 //  * floating pieces (FP16X3): t = x 2^(14-e) = h + l, h = fp16(t),
 //    l = fp16(t - h); accumulation rounding is not exact.
 #pragma once
@@ -27,6 +28,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "tc.cuh"
 #include "tc_host.cuh"
 
@@ -35,7 +37,6 @@ namespace distil {
 struct Scheme {
   bool bf16, fixed;
   int H, W;    // fixed point: t = x 2^(H - e), slices of W bits; floating: H = 14
-               // (H of the mode contractions; the elementals use H - 1)
   int na, nb;  // pieces of the A / B operand
   int nprod;
   int pa[6], pb[6], acc[6];
@@ -67,10 +68,10 @@ inline void fill_products(tc::GemmCfg& cfg, const Scheme& s) {
 }
 
 // Exponent e with max |x| < 2^e (0 for an all-zero row).
-__device__ __forceinline__ int row_exponent_d(double m) {
-  if (!(m > 0.0) || !isfinite(m)) return 0;
+__device__ __forceinline__ int row_exponent(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return 0;
   int e;
-  frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+  frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
   return e;
 }
 
@@ -80,29 +81,30 @@ struct SliceBits {
   static constexpr int W = BF16 ? 8 : 11;
 };
 
-// NPC pieces of x (given in double so that results of an FP64 epilogue
-// keep all their bits) for a row with exponent e and leading-slice width
-// H (scheme notes above).
+// NPC pieces of the double-float x for a row with exponent e and leading
+// slice width H (scheme notes above), in FP32 instructions: scaling by
+// powers of two is exact, t.hi - rint(t.hi) is exact, and adding t.lo to
+// that remainder rounds far below the last slice.
 template <bool BF16, bool FIXED, int NPC>
-__device__ __forceinline__ void make_pieces(double x, int e, int H, typename tc::Piece<BF16>::T (&p)[NPC]) {
+__device__ __forceinline__ void make_pieces(DF x, int e, int H, typename tc::Piece<BF16>::T (&p)[NPC]) {
   using PC = tc::Piece<BF16>;
   constexpr int W = SliceBits<BF16>::W;
   if constexpr (FIXED) {
-    constexpr double sw = (double)(1 << W), isw = 1.0 / (double)(1 << W);
-    const double t = ldexp(x, H - e);
-    const double hi = rint(t);
-    const double r1 = (t - hi) * sw;
-    const double mid = rint(r1);
-    const double lo = rint((r1 - mid) * sw);
-    p[0] = PC::from((float)hi);
-    if constexpr (NPC >= 2) p[1] = PC::from((float)mid);
-    if constexpr (NPC == 3) p[2] = PC::from((float)(lo * isw));
+    constexpr float sw = (float)(1 << W), isw = 1.f / (float)(1 << W);
+    const float th = ldexpf(x.hi, H - e), tl = ldexpf(x.lo, H - e);
+    const float hi = rintf(th);
+    const float r1 = __fmul_rn(__fadd_rn(__fsub_rn(th, hi), tl), sw);
+    const float mid = rintf(r1);
+    const float lo = rintf(__fmul_rn(__fsub_rn(r1, mid), sw));
+    p[0] = PC::from(hi);
+    if constexpr (NPC >= 2) p[1] = PC::from(mid);
+    if constexpr (NPC == 3) p[2] = PC::from(lo * isw);
     if constexpr (NPC == 4) {
-      p[2] = PC::from((float)(mid * isw));
-      p[3] = PC::from((float)(lo * isw));
+      p[2] = PC::from(mid * isw);
+      p[3] = PC::from(lo * isw);
     }
   } else {
-    float t = (float)ldexp(x, H - e);
+    float t = ldexpf(x.hi, H - e) + ldexpf(x.lo, H - e);
 #pragma unroll
     for (int i = 0; i < NPC; ++i) {
       p[i] = PC::from(t);
@@ -114,9 +116,10 @@ __device__ __forceinline__ void make_pieces(double x, int e, int H, typename tc:
 // Split rows of a complex operand into 2*NPC planes with a per-row exponent.
 // Global row r = coord * rows_per + rr goes to
 //   out[coord][plane][rr][k]  (plane stride rows_per*ld, coord stride 2*NPC*rows_per*ld)
-// and exps[r].  One warp per row: pass 1 finds max |re|, |im| over the row,
-// pass 2 writes the pieces.  Src::operator()(r, k) returns the element.
-// Optionally also the row's 2-norm sqrt(sum |x|^2) into norms[r].
+// and exps[r]; optionally the row's 2-norm (with a small safety margin)
+// into norms[r].  One warp per row: pass 1 finds max |re|, |im| over the
+// row, pass 2 writes the pieces.  Src::operator()(r, k) returns the element
+// as a complex double-float.
 template <bool BF16, bool FIXED, int NPC, class Src>
 __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, long long rows_per, int K, int H,
                                                          typename tc::Piece<BF16>::T* __restrict__ out, long long ld,
@@ -125,29 +128,30 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= nrows) return;
-  double m = 0.0, ss = 0.0;
+  float m = 0.f, ss = 0.f;
   for (int k = lane; k < K; k += 32) {
-    const double2 v = src(r, k);
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
-    ss += v.x * v.x + v.y * v.y;
+    const CDF v = src(r, k);
+    m = fmaxf(m, fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
+    ss = fmaf(v.re.hi, v.re.hi, fmaf(v.im.hi, v.im.hi, ss));
   }
   for (int o = 16; o > 0; o >>= 1) {
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     ss += __shfl_xor_sync(0xffffffffu, ss, o);
   }
-  const int e = row_exponent_d(m);
+  // a rounded hi part may sit just below the true magnitude: pad by 2^-20
+  const int e = row_exponent(m * (1.f + 1.f / 1048576.f));
   if (lane == 0) {
     exps[r] = e;
-    if (norms) norms[r] = (float)(sqrt(ss) * (1.0 + 1e-6));
+    if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
   }
   const long long coord = r / rows_per, rr = r % rows_per;
   const long long ps = rows_per * ld;
   P16* base = out + coord * (2 * NPC) * ps + rr * ld;
   for (int k = lane; k < K; k += 32) {
-    const double2 v = src(r, k);
+    const CDF v = src(r, k);
     P16 pr[NPC], pi[NPC];
-    make_pieces<BF16, FIXED, NPC>(v.x, e, H, pr);
-    make_pieces<BF16, FIXED, NPC>(v.y, e, H, pi);
+    make_pieces<BF16, FIXED, NPC>(v.re, e, H, pr);
+    make_pieces<BF16, FIXED, NPC>(v.im, e, H, pi);
 #pragma unroll
     for (int i = 0; i < NPC; ++i) {
       base[(2 * i) * ps + k] = pr[i];
@@ -185,27 +189,46 @@ struct ColMap {
   }
 };
 
-// out[batch][row * sr + colmap(col)] = D, stored as complex64 (OUT = float2)
-// or complex128 (OUT = double2); two-level batch offset.
-template <class OUT>
-struct EpiStore {
-  OUT* out;
+// The GEMM hands the epilogue each value as an unevaluated FP32 pair
+// (leading-slice part, cross-term part): D = re0 + re1, im0 + im1.
+
+// out[batch][row * sr + colmap(col)] = D as a complex double-float.
+struct EpiStoreCDF {
+  CDF* out;
   long long sb_hi, sb_lo;
   int b_lo;
   long long sr;
   ColMap cm;
   int N;
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const double* re, const double* im) const {
-    OUT* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
+  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
+                                             const float* im0, const float* im1) const {
+    CDF* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int c = col0 + e;
       if (c >= N) break;
-      OUT v;
-      v.x = re[e];
-      v.y = im[e];
-      base[cm(c)] = v;
+      base[cm(c)] = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
+    }
+  }
+};
+
+// out[batch][row][col] = D rounded to complex64 (public split GEMM).
+struct EpiStoreC64 {
+  float2* out;
+  long long sb;
+  long long sr;
+  int N;
+  __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
+  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
+                                             const float* im0, const float* im1) const {
+    float2* base = out + (long long)batch * sb + (long long)row * sr;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int c = col0 + e;
+      if (c >= N) break;
+      const DF r = two_sum(re0[e], re1[e]), i = two_sum(im0[e], im1[e]);
+      base[c] = make_float2(r.hi, i.hi);
     }
   }
 };

@@ -1,8 +1,14 @@
 // Mixed-precision correlation matrix: the three mode contractions of
 // correlate.cuh on tcgen05 tensor cores with operands split into 16-bit
 // pieces with per-row power-of-two exponents (mixed_common.cuh), FP32
-// accumulation in TMEM combined in FP64, FP64 intermediates between the
-// contractions, and the final dot accumulated in FP64.
+// accumulation in TMEM, double-float intermediates between the contractions
+// and a double-float dot whose block sums are added into C in FP64.
+//
+// Every (t, p) is first normalised: tau(t) by 2^-e_tau(t), Phi_snk(t,p) by
+// 2^-e_snk, Phi_src(p) by 2^-e_src (exponents of their largest entries), so
+// every intermediate stays well inside the FP32 range however fast tau
+// decays with t; C picks the factor 2^(3 e_tau + e_snk + e_src) back up in
+// FP64.
 //
 // Per (t, p):
 //   split    Aa  rows (a'beta, i')  K i        from Gamma_beta tau[(alpha(beta) i)][(a' i')]
@@ -13,11 +19,11 @@
 //   step i   U[a][a'][(i',k)][(beta,j)] = sum_i Aa G, split by the epilogue
 //            with the row exponent of the Cauchy-Schwarz bound
 //            |U| <= max_beta |Aa row| * max_j |G row|
-//   step j   V[a][slot][j'][(i',k)]     = sum_(beta,j) U tauT        (complex128)
-//   source   X[b][c][pair][k]           = sum_k' S Tc                (complex128)
-//   dot      C_ab                         (dot.cuh)
+//   step j   V[a][slot][j'][(i',k)]     = sum_(beta,j) U tauT
+//   source   X[b][c][pair][k]           = sum_k' S Tc
+//   dot      C_ab
 #include "correlate.cuh"
-#include "dot.cuh"
+#include "df.cuh"
 #include "mixed.cuh"
 #include "mixed_common.cuh"
 
@@ -25,76 +31,132 @@ namespace distil {
 
 using tc::Planes;
 
-// ------------------------------------------------------------------ sources
-__device__ __forceinline__ double2 d2(float2 x) { return make_double2(x.x, x.y); }
+// ------------------------------------------------------------------ setup
+// binary exponent e with |x| < 2^e for the largest |component| of a complex128
+// array, from the bit patterns (no FP64 arithmetic)
+__device__ __forceinline__ int dbl_exp_bound(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  return ex == 0 ? -1022 : ex - 1022;  // |x| < 2^(ex - 1023 + 1)
+}
+// exps[i] for array i of `count` arrays of `len` complex128 values
+__global__ void c128_exp_kernel(const double2* __restrict__ x, long long len, int* __restrict__ exps) {
+  const double2* a = x + (long long)blockIdx.x * len;
+  int m = -1022;
+  for (long long e = threadIdx.x; e < len; e += blockDim.x) {
+    m = max(m, max(dbl_exp_bound(a[e].x), dbl_exp_bound(a[e].y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ int red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    exps[blockIdx.x] = max(m, red[0]);
+  }
+}
+// exps[i] with max |x| < 2^exps[i] for complex64 array i
+__global__ void c64_exp_kernel(const float2* __restrict__ x, long long len, int* __restrict__ exps) {
+  const float2* a = x + (long long)blockIdx.x * len;
+  float m = 0.f;
+  for (long long e = threadIdx.x; e < len; e += blockDim.x) m = fmaxf(m, fmaxf(fabsf(a[e].x), fabsf(a[e].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    exps[blockIdx.x] = row_exponent(m);
+  }
+}
+// complex128 -> complex double-float, times 2^-e (one exponent per array)
+__global__ void c128_to_cdf_kernel(const double2* __restrict__ x, long long len, const int* __restrict__ exps,
+                                   CDF* __restrict__ out) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  const double s = ldexp(1.0, -exps[0]);
+  const double2 v = x[e];
+  out[e] = cdf_make(df_from_double(v.x * s), df_from_double(v.y * s));
+}
+__global__ void prof_to_df_kernel(const double* __restrict__ g, long long n, DF* __restrict__ out) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n) out[e] = df_from_double(g[e]);
+}
 
+// ------------------------------------------------------------------ sources
+__device__ __forceinline__ CDF cdf_of(float2 x, float s) {
+  return cdf_make(df_make(x.x * s, 0.f), df_make(x.y * s, 0.f));
+}
 struct AaSrc {  // rows (a'*4 + beta)*n + i', K = i
   const float2* tau;
+  const int* etau;
   int n;
-  __device__ __forceinline__ double2 operator()(long long r, int i) const {
+  __device__ __forceinline__ CDF operator()(long long r, int i) const {
     const int ab = (int)(r / n), ip = (int)(r % n);
     const int ap = ab >> 2, beta = ab & 3, alpha = beta ^ 1;
-    const float2 x = tau[((long long)alpha * n + i) * 4 * n + ap * n + ip];
     // Gamma_{10} = Gamma_{32} = +1, Gamma_{01} = Gamma_{23} = -1
-    return (beta & 1) ? make_double2(-x.x, -x.y) : d2(x);
+    const float s = (beta & 1) ? -tc::pow2f(-etau[0]) : tc::pow2f(-etau[0]);
+    return cdf_of(tau[((long long)alpha * n + i) * 4 * n + ap * n + ip], s);
   }
 };
 struct TTSrc {  // rows (b'j'), K = (beta j): tau^T
   const float2* tau;
+  const int* etau;
   int n;
-  __device__ __forceinline__ double2 operator()(long long r, int k) const {
-    return d2(tau[(long long)k * 4 * n + r]);
+  __device__ __forceinline__ CDF operator()(long long r, int k) const {
+    return cdf_of(tau[(long long)k * 4 * n + r], tc::pow2f(-etau[0]));
   }
 };
 struct TcSrc {  // rows c*n + k, K = k': T^c[k][k']
   const float2* tau;
+  const int* etau;
   int n;
-  __device__ __forceinline__ double2 operator()(long long r, int kp) const {
+  __device__ __forceinline__ CDF operator()(long long r, int kp) const {
     const int c = (int)(r / n), k = (int)(r % n);
     const long long n4 = 4LL * n;
+    const float s = tc::pow2f(-etau[0]);
     if (c == 0) {
       const float2 a = tau[(long long)k * n4 + kp], b = tau[((long long)n + k) * n4 + n + kp];
-      return make_double2((double)a.x + b.x, (double)a.y + b.y);
+      return cdf_make(two_sum(a.x * s, b.x * s), two_sum(a.y * s, b.y * s));
     }
     const int mu = (c <= 2) ? 0 : 1;
     const int gp = (c == 1 || c == 3) ? 2 : 3;
-    return d2(tau[((long long)mu * n + k) * n4 + gp * n + kp]);
+    return cdf_of(tau[((long long)mu * n + k) * n4 + gp * n + kp], s);
   }
 };
 // sorted-triple lookup with sign; 0 on a repeated index
-__device__ __forceinline__ double2 phi_at(const double2* phi, int i, int j, int k, double w) {
-  if (i == j || j == k || i == k) return make_double2(0.0, 0.0);
+__device__ __forceinline__ CDF phi_at(const CDF* phi, int i, int j, int k, DF w) {
+  if (i == j || j == k || i == k) return cdf_zero();
   int x = i, y = j, z = k;
-  if (x > y) { int t = x; x = y; y = t; w = -w; }
-  if (y > z) { int t = y; y = z; z = t; w = -w; }
-  if (x > y) { int t = x; x = y; y = t; w = -w; }
-  const double2 p = phi[triple_rank(x, y, z)];
-  return make_double2(p.x * w, p.y * w);
+  bool neg = false;
+  if (x > y) { int t = x; x = y; y = t; neg = !neg; }
+  if (y > z) { int t = y; y = z; z = t; neg = !neg; }
+  if (x > y) { int t = x; x = y; y = t; neg = !neg; }
+  return cdf_scale(phi[triple_rank(x, y, z)], neg ? df_neg(w) : w);
 }
 struct GSrc {  // rows a*n^2 + k*n + j, K = i: g_i g_j g_k Phi_ijk
-  const double2* phi;
-  const double* g;
+  const CDF* phi;
+  const DF* g;
   int n;
-  __device__ __forceinline__ double2 operator()(long long r, int i) const {
+  __device__ __forceinline__ CDF operator()(long long r, int i) const {
     const long long n2 = (long long)n * n;
     const int a = (int)(r / n2);
     const int k = (int)((r % n2) / n), j = (int)(r % n);
-    const double* ga = g + (long long)a * n;
-    return phi_at(phi, i, j, k, ga[i] * ga[j] * ga[k]);
+    const DF* ga = g + (long long)a * n;
+    return phi_at(phi, i, j, k, df_mul(df_mul(ga[i], ga[j]), ga[k]));
   }
 };
 struct SSrc {  // rows b*P2 + pair(i'<j'), K = k': g g g conj(Phi_{i'j'k'})
-  const double2* phi;
-  const double* g;
+  const CDF* phi;
+  const DF* g;
   int n;
   long long P2;
-  __device__ __forceinline__ double2 operator()(long long r, int kp) const {
+  __device__ __forceinline__ CDF operator()(long long r, int kp) const {
     const int b = (int)(r / P2);
     int ip, jp;
     pair_unrank(r % P2, ip, jp);
-    const double* gb = g + (long long)b * n;
-    const double2 v = phi_at(phi, ip, jp, kp, gb[ip] * gb[jp] * gb[kp]);
-    return make_double2(v.x, -v.y);
+    const DF* gb = g + (long long)b * n;
+    return cdf_conj(phi_at(phi, ip, jp, kp, df_mul(df_mul(gb[ip], gb[jp]), gb[kp])));
   }
 };
 
@@ -112,11 +174,11 @@ __global__ void u_exponent_kernel(const float* __restrict__ nAa, const float* __
   float mG = 0.f;
   const float* g = nG + (long long)a * n2 + (long long)k * n;
   for (int j = 0; j < n; ++j) mG = fmaxf(mG, g[j]);
-  eU[e] = row_exponent_d((double)mA * (double)mG * (1.0 + 1e-5));
+  eU[e] = row_exponent(mA * mG * (1.f + 1e-5f));
 }
 
-// Step i epilogue: split U straight from the FP64-combined accumulators into
-// the A-operand pieces of step j, U[(a,a')][plane][(i',k)][(beta,j)].
+// Step i epilogue: split U straight from the accumulator pair into the
+// A-operand pieces of step j, U[(a,a')][plane][(i',k)][(beta,j)].
 template <bool BF16, bool FIXED, int NPC>
 struct EpiSplitU {
   typename tc::Piece<BF16>::T* out;
@@ -124,8 +186,8 @@ struct EpiSplitU {
   int n, H;
   long long ld4;
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const double* re,
-                                             const double* im) const {
+  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
+                                             const float* im0, const float* im1) const {
     const long long n2 = (long long)n * n;
     const int aa = batch >> 2, beta = batch & 3;  // aa = a*3 + a'
     const long long ps = n2 * ld4;
@@ -138,8 +200,8 @@ struct EpiSplitU {
       const long long ur = (long long)row * n + k;
       const int ex = eU[(long long)aa * n2 + ur];
       typename tc::Piece<BF16>::T pr[NPC], pi[NPC];
-      make_pieces<BF16, FIXED, NPC>(re[e], ex, H, pr);
-      make_pieces<BF16, FIXED, NPC>(im[e], ex, H, pi);
+      make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), ex, H, pr);
+      make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), ex, H, pi);
       auto* d = base + ur * ld4 + (long long)beta * n + j;
 #pragma unroll
       for (int q = 0; q < NPC; ++q) {
@@ -150,17 +212,99 @@ struct EpiSplitU {
   }
 };
 
+// ------------------------------------------------------------------ dot
+// accumulate a * b (double-floats) into the unevaluated pair (s, c)
+__device__ __forceinline__ void df_acc_prod(float& s, float& c, DF a, DF b) {
+  const DF p = two_prod(a.hi, b.hi);
+  const DF t = two_sum(s, p.hi);
+  s = t.hi;
+  c += t.lo + __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+}
+
+// C[q][a][b][t] += 2^scale sum_terms coef sum_{i'<j',k} (V^a_{i'j'k} - V^a_{j'i'k}) X^{b,c}_{pair,k}
+// V[a][slot][j'][i'][k], X[b][c][pair][k] (double-floats); block = (a, chunk of pairs).
+template <int MAXB>
+__global__ void __launch_bounds__(256)
+dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int nb, const int* __restrict__ etau,
+              const int* __restrict__ esnk, const int* __restrict__ esrc, Cx<double>* __restrict__ C,
+              long long cstride_a, long long cstride_b) {
+  const int a = blockIdx.y;
+  const long long P2 = comb2(nv);
+  const long long n3 = (long long)nv * nv * nv;
+  const long long work = P2 * nv;
+  float sr[MAXB], cr[MAXB], si[MAXB], ci[MAXB];
+#pragma unroll
+  for (int b = 0; b < MAXB; ++b) sr[b] = cr[b] = si[b] = ci[b] = 0.f;
+  const CDF* Va = V + (long long)a * NPAIR * n3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < work;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e / nv;
+    const int k = (int)(e % nv);
+    int ip, jp;
+    pair_unrank(q, ip, jp);
+    CDF w[NTERM];
+#pragma unroll
+    for (int t = 0; t < NTERM; ++t) {
+      const CDF* Vs = Va + dot_slot(t) * n3;
+      const CDF d = cdf_sub(Vs[((long long)jp * nv + ip) * nv + k], Vs[((long long)ip * nv + jp) * nv + k]);
+      const float cf = (float)dot_coef(t);
+      w[t] = cdf_make(df_mul_f(d.re, cf), df_mul_f(d.im, cf));
+    }
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      if (b >= nb) break;
+      const CDF* Xb = X + (long long)b * NSRC * work;
+#pragma unroll
+      for (int t = 0; t < NTERM; ++t) {
+        const CDF x = Xb[dot_src(t) * work + e];
+        df_acc_prod(sr[b], cr[b], w[t].re, x.re);
+        df_acc_prod(sr[b], cr[b], df_neg(w[t].im), x.im);
+        df_acc_prod(si[b], ci[b], w[t].re, x.im);
+        df_acc_prod(si[b], ci[b], w[t].im, x.re);
+      }
+    }
+  }
+  __shared__ double red[2][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double scale = ldexp(1.0, 3 * etau[0] + esnk[0] + esrc[0]);
+  for (int b = 0; b < nb && b < MAXB; ++b) {
+    DF vr = two_sum(sr[b], cr[b]), vi = two_sum(si[b], ci[b]);
+    for (int o = 16; o > 0; o >>= 1) {
+      vr = df_add(vr, df_make(__shfl_xor_sync(0xffffffffu, vr.hi, o), __shfl_xor_sync(0xffffffffu, vr.lo, o)));
+      vi = df_add(vi, df_make(__shfl_xor_sync(0xffffffffu, vi.hi, o), __shfl_xor_sync(0xffffffffu, vi.lo, o)));
+    }
+    if (lane == 0) {
+      red[0][wid] = df_to_double(vr);
+      red[1][wid] = df_to_double(vi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double zr = 0.0, zi = 0.0;
+      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) {
+        zr += red[0][u];
+        zi += red[1][u];
+      }
+      double* dst = reinterpret_cast<double*>(C + a * cstride_a + b * cstride_b);
+      atomicAdd(dst, zr * scale);
+      atomicAdd(dst + 1, zi * scale);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ workspace
 struct MixedWs {
   void *Aa, *TT, *Tc, *G, *S, *U;
   int *eAa, *eTT, *eTc, *eG, *eS, *eU;
   float *nAa, *nG;
-  Cx<double>*V, *X;
+  CDF *V, *X, *phs, *ph0;
+  DF* g;
+  int *etau, *esnk, *esrc;
   long long ldn, ld4;
 };
 
-static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nv, int nb) {
-  const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv);
+static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, int nb) {
+  const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv), T3 = comb3(nv);
   const int npa = 2 * sc.na, npb = 2 * sc.nb;
   MixedWs w;
   w.ldn = tc::pad64(n);
@@ -179,14 +323,20 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nv, int nb) {
   w.eU = ar.take<int>(3 * nb * n2);
   w.nAa = ar.take<float>(12 * n);
   w.nG = ar.take<float>(nb * n2);
-  w.V = ar.take<Cx<double>>((long long)nb * NPAIR * n3);
-  w.X = ar.take<Cx<double>>((long long)nb * NSRC * P2 * n);
+  w.V = ar.take<CDF>((long long)nb * NPAIR * n3);
+  w.X = ar.take<CDF>((long long)nb * NSRC * P2 * n);
+  w.phs = ar.take<CDF>(T3);
+  w.ph0 = ar.take<CDF>(T3);
+  w.g = ar.take<DF>((long long)(nt + 1) * nb * n);
+  w.etau = ar.take<int>(nt);
+  w.esnk = ar.take<int>((long long)nt * np);
+  w.esrc = ar.take<int>(np);
   return w;
 }
 
-size_t correlate_mixed_workspace(int mode, int nv, int nb) {
+size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
   Arena ar;
-  carve_mixed(ar, scheme_of(mode), nv, nb);
+  carve_mixed(ar, scheme_of(mode), nt, nv, np, nb);
   return ar.used + 256;
 }
 
@@ -202,22 +352,31 @@ static int gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
   return tc::launch_gemm<32, KC, NPLA, NPLB, 2, BF16>(ctx, name, A, B, cfg, batch, epi, s);
 }
 
+static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
+
 template <bool BF16, bool FIXED, int NA, int NB>
-static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs, const double2* ph0,
-                        const float2* tau, const double* g_snk, const double* g_src, int nv, int nb,
-                        const MixedWs& w, Cx<double>* Cout, long long cs_a, long long cs_b, cudaStream_t s) {
+static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c128, const double2* ph0_c128,
+                        const float2* tau, const DF* g_snk, const DF* g_src, const int* etau, const int* esnk,
+                        const int* esrc, int nv, int nb, const MixedWs& w, Cx<double>* Cout, long long cs_a,
+                        long long cs_b, cudaStream_t s) {
   constexpr int NPLA = 2 * NA, NPLB = 2 * NB;
-  const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv);
+  const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv), T3 = comb3(nv);
   using P16 = typename tc::Piece<BF16>::T;
+  {
+    Launch L(ctx, "normalise", s);
+    c128_to_cdf_kernel<<<nblk(T3), 256, 0, s>>>(phs_c128, T3, esnk, w.phs);
+    c128_to_cdf_kernel<<<nblk(T3), 256, 0, s>>>(ph0_c128, T3, esrc, w.ph0);
+  }
   // ---- split operands (one warp per row, per-row exponents)
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, AaSrc{tau, nv}, 12 * n, n, nv, sch.H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TTSrc{tau, nv}, 4 * n, 4 * n, 4 * nv, sch.H, w.TT, w.ld4, w.eTT, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TcSrc{tau, nv}, 5 * n, n, nv, sch.H, w.Tc, w.ldn, w.eTc, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, GSrc{phs, g_snk, nv}, nb * n2, n2, nv, sch.H, w.G, w.ldn, w.eG, s, w.nG)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, SSrc{ph0, g_src, nv, P2}, nb * P2, P2, nv, sch.H, w.S, w.ldn, w.eS, s)));
+  const int H = sch.H;
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, AaSrc{tau, etau, nv}, 12 * n, n, nv, H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TTSrc{tau, etau, nv}, 4 * n, 4 * n, 4 * nv, H, w.TT, w.ld4, w.eTT, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TcSrc{tau, etau, nv}, 5 * n, n, nv, H, w.Tc, w.ldn, w.eTc, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, GSrc{w.phs, g_snk, nv}, nb * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, SSrc{w.ph0, g_src, nv, P2}, nb * P2, P2, nv, H, w.S, w.ldn, w.eS, s)));
   {
     Launch L(ctx, "u_exponent", s);
-    u_exponent_kernel<<<(unsigned)((3 * nb * n2 + 255) / 256), 256, 0, s>>>(w.nAa, w.nG, nv, nb, w.eU);
+    u_exponent_kernel<<<nblk(3 * nb * n2), 256, 0, s>>>(w.nAa, w.nG, nv, nb, w.eU);
   }
   DISTIL_LAUNCH_CHECK();
 
@@ -232,7 +391,7 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs, 
     cfg.M = nv; cfg.N = (int)n2; cfg.K = nv;
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
     cfg.b = tc::OpMap{12, nb, 1, 0, 0, (int)n2, w.eG};
-    EpiSplitU<BF16, FIXED, NA> epi{(P16*)w.U, w.eU, nv, sch.H, w.ld4};
+    EpiSplitU<BF16, FIXED, NA> epi{(P16*)w.U, w.eU, nv, H, w.ld4};
     DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
   }
   // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
@@ -243,8 +402,8 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs, 
     cfg.M = (int)n2; cfg.N = (3 - ap) * nv; cfg.K = 4 * nv;
     cfg.a = tc::OpMap{1, nb, 3, ap, 0, (int)n2, w.eU};
     cfg.b = tc::OpMap{1, 1, 0, 0, (ap + 1) * nv, 4 * nv, w.eTT};
-    EpiStore<double2> epi;
-    epi.out = reinterpret_cast<double2*>(w.V + (long long)slotbase[ap] * n3);
+    EpiStoreCDF epi;
+    epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
     DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
@@ -256,8 +415,8 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs, 
     cfg.M = (int)P2; cfg.N = nv; cfg.K = nv;
     cfg.a = tc::OpMap{NSRC, nb, 1, 0, 0, (int)P2, w.eS};
     cfg.b = tc::OpMap{1, NSRC, 1, 0, 0, nv, w.eTc};
-    EpiStore<double2> epi;
-    epi.out = reinterpret_cast<double2*>(w.X);
+    EpiStoreCDF epi;
+    epi.out = w.X;
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
     epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
     DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
@@ -265,10 +424,10 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs, 
   // ---- dot
   {
     long long work = P2 * n;
-    unsigned gx = (unsigned)((work + 255) / 256);
-    if (gx > 1024) gx = 1024;
+    unsigned gx = nblk(work);
+    if (gx > 592) gx = 592;
     Launch L(ctx, "dot", s);
-    dot_kernel<double, 16><<<dim3(gx, nb), 256, 0, s>>>(w.V, w.X, nv, nb, Cout, cs_a, cs_b);
+    dot_df_kernel<16><<<dim3(gx, nb), 256, 0, s>>>(w.V, w.X, nv, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
@@ -283,30 +442,43 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   if (nv < 3) return DISTIL_OK;
   const Scheme sch = scheme_of(mode);
   Arena ar(ws, ws_bytes);
-  MixedWs w = carve_mixed(ar, sch, nv, nb);
+  MixedWs w = carve_mixed(ar, sch, nt, nv, np, nb);
   if (!ar.fits()) {
     set_error("correlate: workspace too small");
     return DISTIL_ENOMEM;
   }
   const long long T3 = comb3(nv), n4 = 4LL * nv;
+  const long long nprof = (prof_per_t ? (long long)nt : 1) * nb * nv;
+  {
+    Launch L(ctx, "normalise", s);
+    c64_exp_kernel<<<nt, 256, 0, s>>>((const float2*)tau, n4 * n4, w.etau);
+    c128_exp_kernel<<<nt * np, 256, 0, s>>>((const double2*)phi_snk, T3, w.esnk);
+    c128_exp_kernel<<<np, 256, 0, s>>>((const double2*)phi_src, T3, w.esrc);
+    prof_to_df_kernel<<<nblk(nprof), 256, 0, s>>>(prof, nprof, w.g);
+  }
+  DISTIL_LAUNCH_CHECK();
   Cx<double>* Cd = reinterpret_cast<Cx<double>*>(C);
   for (int t = 0; t < nt; ++t) {
-    const double* g_snk = prof + (prof_per_t ? (long long)t * nb * nv : 0);
+    const DF* g_snk = w.g + (prof_per_t ? (long long)t * nb * nv : 0);
     for (int q = 0; q < np; ++q) {
       const double2* phs = (const double2*)phi_snk + ((long long)t * np + q) * T3;
       const double2* ph0 = (const double2*)phi_src + (long long)q * T3;
       const float2* ta = (const float2*)tau + (long long)t * n4 * n4;
       Cx<double>* Cq = Cd + (long long)q * nb * nb * nt + t;
       const long long ca = (long long)nb * nt, cb = nt;
+      const int* et = w.etau + t;
+      const int* es = w.esnk + (long long)t * np + q;
+      const int* e0 = w.esrc + q;
       int st;
       if (mode == DISTIL_MIXED_FP16X6)
-        st = run_tp_mixed<false, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<false, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb, s);
       else if (mode == DISTIL_MIXED_BF16X6)
-        st = run_tp_mixed<true, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<true, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb, s);
       else if (mode == DISTIL_MIXED_BF16X3)
-        st = run_tp_mixed<true, true, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<true, true, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb, s);
       else
-        st = run_tp_mixed<false, false, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, prof, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<false, false, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb,
+                                              s);
       if (st != DISTIL_OK) return st;
     }
   }

@@ -5,14 +5,16 @@
 //
 // per timeslice as one complex GEMM with M = pairs j<k (ordered by j, then
 // k), N = (i, q) rows and K = (site, colour).  K is cut into chunks of
-// EL_KC values: per chunk the operands are formed in FP64 from the
-// eigenvectors and split into 16-bit pieces with per-(row, chunk) exponents,
-// the tensor cores accumulate the chunk in TMEM (the leading fixed-point
-// slice exactly), and the epilogue adds the chunk into an FP64 accumulator
+// EL_KC values: per chunk the operands are formed from the eigenvectors in
+// double-float arithmetic (the cross products exactly, by TwoProduct) and
+// split into 16-bit pieces with per-(row, chunk) exponents; the tensor
+// cores accumulate the chunk in TMEM (the leading fixed-point slice
+// exactly), and the epilogue adds the chunk into a double-float accumulator
 // Phi_acc[pair][(i,q)].  Tiles whose every i is >= every j are skipped.  A
-// final pass packs i<j<k into Phi[t][q][rank].
+// final pass packs i<j<k into Phi[t][q][rank] as complex128.
 #include <math.h>
 
+#include "df.cuh"
 #include "elementals.cuh"
 #include "mixed.cuh"
 #include "mixed_common.cuh"
@@ -22,7 +24,7 @@ namespace distil {
 using tc::Planes;
 
 constexpr int EL_KC = 4096;  // K values per accumulation chunk
-constexpr int EL_H = 10;     // leading-slice width of the elemental operands (FP16)
+constexpr int EL_H = 10;     // leading-slice width of the FP16 elemental operands
 
 // pairs in j-major order: q -> (j, k), first index j, then k = j+1..n-1
 __host__ __device__ __forceinline__ long long jmajor_first(long long j, long long n) { return j * (2 * n - j - 1) / 2; }
@@ -30,20 +32,21 @@ __global__ void pair_table_kernel(int n, int2* pairs) {
   const long long P2 = comb2(n);
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= P2) return;
-  const double b = 2.0 * n - 1.0;
-  long long j = (long long)floor((b - sqrt(b * b - 8.0 * (double)q)) * 0.5);
+  const float b = 2.f * n - 1.f;
+  long long j = (long long)floorf((b - sqrtf(fmaxf(b * b - 8.f * (float)q, 0.f))) * 0.5f);
   if (j < 0) j = 0;
   while (j > 0 && jmajor_first(j, n) > q) --j;
   while (jmajor_first(j + 1, n) <= q) ++j;
   pairs[q] = make_int2((int)j, (int)(q - jmajor_first(j, n) + j + 1));
 }
 
-__global__ void phase_table_kernel(int L, double2* tab) {
+// exp(-2 pi i m / L) as double-floats
+__global__ void phase_table_kernel(int L, CDF* tab) {
   const int m = threadIdx.x + blockIdx.x * blockDim.x;
   if (m >= L) return;
   double s, c;
   sincospi(2.0 * (double)m / (double)L, &s, &c);
-  tab[m] = make_double2(c, -s);  // exp(-2 pi i m / L)
+  tab[m] = cdf_make(df_from_double(c), df_from_double(-s));
 }
 
 struct MomArgs {
@@ -51,33 +54,38 @@ struct MomArgs {
   int mom[EL_MAX_MOM][3];
 };
 
+// a*b - c*d for complex FP32 inputs, exactly products then double-float sums
+__device__ __forceinline__ DF dot2_sub(float a, float b, float c, float d) {
+  return df_sub(two_prod(a, b), two_prod(c, d));
+}
 struct WSrc {  // rows q (pairs), K = (x, a) from K0
   const float2* v;  // v[t] = [n][V3][3]
   const int2* pairs;
   long long V3;
   long long K0;
-  __device__ __forceinline__ double2 operator()(long long q, int kk) const {
+  __device__ __forceinline__ CDF operator()(long long q, int kk) const {
     const long long K = K0 + kk;
     const long long x = K / 3;
     const int a = (int)(K % 3), b = (a + 1) % 3, c = (a + 2) % 3;
     const int2 jk = pairs[q];
     const float2* vj = v + ((long long)jk.x * V3 + x) * 3;
     const float2* vk = v + ((long long)jk.y * V3 + x) * 3;
-    const double2 jb = make_double2(vj[b].x, vj[b].y), jc = make_double2(vj[c].x, vj[c].y);
-    const double2 kb = make_double2(vk[b].x, vk[b].y), kc = make_double2(vk[c].x, vk[c].y);
+    const float2 jb = vj[b], jc = vj[c], kb = vk[b], kc = vk[c];
     // w^a = v_j^b v_k^c - v_j^c v_k^b
-    return make_double2(jb.x * kc.x - jb.y * kc.y - (jc.x * kb.x - jc.y * kb.y),
-                        jb.x * kc.y + jb.y * kc.x - (jc.x * kb.y + jc.y * kb.x));
+    const DF re = df_sub(dot2_sub(jb.x, kc.x, jb.y, kc.y), dot2_sub(jc.x, kb.x, jc.y, kb.y));
+    const DF im = df_sub(df_add(two_prod(jb.x, kc.y), two_prod(jb.y, kc.x)),
+                         df_add(two_prod(jc.x, kb.y), two_prod(jc.y, kb.x)));
+    return cdf_make(re, im);
   }
 };
 
 struct ESrc {  // rows i*np + q, K = (x, a) from K0
   const float2* v;
-  const double2* tab;
+  const CDF* tab;
   MomArgs m;
   long long V3;
   long long K0;
-  __device__ __forceinline__ double2 operator()(long long r, int kk) const {
+  __device__ __forceinline__ CDF operator()(long long r, int kk) const {
     const long long K = K0 + kk;
     const long long x = K / 3;
     const int a = (int)(K % 3);
@@ -85,16 +93,17 @@ struct ESrc {  // rows i*np + q, K = (x, a) from K0
     const int L = m.L;
     const int xs = (int)(x % L), ys = (int)((x / L) % L), zs = (int)(x / ((long long)L * L));
     const int ph = (m.mom[q][0] * xs + m.mom[q][1] * ys + m.mom[q][2] * zs) % L;
-    const double2 e = tab[ph];
+    const CDF e = tab[ph];
     const float2 u = v[((long long)i * V3 + x) * 3 + a];
-    return make_double2(e.x * u.x - e.y * u.y, e.x * u.y + e.y * u.x);
+    // (e.re + i e.im)(u.x + i u.y)
+    return cdf_make(df_sub(df_mul_f(e.re, u.x), df_mul_f(e.im, u.y)), df_add(df_mul_f(e.re, u.y), df_mul_f(e.im, u.x)));
   }
 };
 
 // Phi_acc[q][r] (+)= D for the pair rows q and (i, q') columns r; the first
 // chunk stores.  Tiles with min i >= max j hold no kept output.
 struct EpiPhiAcc {
-  double2* acc;
+  CDF* acc;
   const int2* pairs;
   long long P2;
   int N, np, first, nt;  // nt: N tile width of the launch
@@ -105,46 +114,43 @@ struct EpiPhiAcc {
     const int imin = (n_tile * nt) / np;   // rows are i * np + q
     return imin >= jmax;
   }
-  __device__ __forceinline__ void operator()(int, int row, int col0, const double* re, const double* im) const {
-    double2* dst = acc + (long long)row * N + col0;
+  __device__ __forceinline__ void operator()(int, int row, int col0, const float* re0, const float* re1,
+                                             const float* im0, const float* im1) const {
+    CDF* dst = acc + (long long)row * N + col0;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       if (col0 + e >= N) break;
-      double2 v = make_double2(re[e], im[e]);
-      if (!first) {
-        const double2 o = dst[e];
-        v.x += o.x;
-        v.y += o.y;
-      }
+      CDF v = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
+      if (!first) v = cdf_add(v, dst[e]);
       dst[e] = v;
     }
   }
 };
 
-// Phi[q][rank(i,j,k)] = Phi_acc[pair(j,k)][i*np + q]
-__global__ void pack_phi_kernel(const double2* __restrict__ acc, int n, int np, double2* __restrict__ phi) {
+// Phi[q][rank(i,j,k)] = Phi_acc[pair(j,k)][i*np + q]  (complex128)
+__global__ void pack_phi_kernel(const CDF* __restrict__ acc, int n, int np, double2* __restrict__ phi) {
   const long long T3 = comb3(n);
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= T3 * np) return;
   const int q = (int)(e / T3);
   const long long r = e % T3;
-  // unrank r -> (i, j, k): k from C(k,3) <= r, then j from C(j,2) <= r - C(k,3)
-  int k = (int)cbrt(6.0 * (double)r) + 1;
-  while (comb3(k) > r) --k;
+  // unrank r -> (i, j, k): k from C(k,3) <= r, then (i, j) from r - C(k,3) = C(j,2) + i
+  int k = (int)cbrtf(6.f * (float)r) + 1;
+  while (k > 2 && comb3(k) > r) --k;
   while (comb3(k + 1) <= r) ++k;
-  const long long r2 = r - comb3(k);
   int j, i;
-  pair_unrank(r2, i, j);  // r2 = C(j,2) + i
+  pair_unrank(r - comb3(k), i, j);
   const long long qp = jmajor_first(j, n) + (k - j - 1);
-  phi[e] = acc[qp * (long long)(n * np) + (long long)i * np + q];
+  const CDF v = acc[qp * (long long)(n * np) + (long long)i * np + q];
+  phi[e] = make_double2(df_to_double(v.re), df_to_double(v.im));
 }
 
 struct ElemWs {
   int2* pairs;
-  double2* tab;
+  CDF* tab;
   void *W, *E;
   int *eW, *eE;
-  double2* acc;
+  CDF* acc;
   long long ldk;
 };
 
@@ -153,12 +159,12 @@ static ElemWs carve_elem(Arena& ar, const Scheme& sc, int L, int nv, int np) {
   ElemWs w;
   w.ldk = tc::pad64(EL_KC);
   w.pairs = ar.take<int2>(P2 > 0 ? P2 : 1);
-  w.tab = ar.take<double2>(L);
+  w.tab = ar.take<CDF>(L);
   w.W = ar.take<uint16_t>(2LL * sc.na * P2 * w.ldk);
   w.E = ar.take<uint16_t>(2LL * sc.nb * R * w.ldk);
   w.eW = ar.take<int>(P2 > 0 ? P2 : 1);
   w.eE = ar.take<int>(R);
-  w.acc = ar.take<double2>(P2 * R);
+  w.acc = ar.take<CDF>(P2 * R);
   return w;
 }
 
@@ -232,9 +238,8 @@ int elementals_mixed(distil_ctx* ctx, const Cx<float>* v, int L, int nt, int nv,
   }
   DISTIL_LAUNCH_CHECK();
   const long long V3 = (long long)L * L * L, T3 = comb3(nv);
-  // the elementals keep their own leading-slice width (long K); floating
-  // pieces keep the scheme's
-  const int H = sch.fixed ? (sch.bf16 ? sch.H : EL_H) : sch.H;
+  // the fixed-point FP16 elementals use their own leading-slice width (long K)
+  const int H = (sch.fixed && !sch.bf16) ? EL_H : sch.H;
   for (int t = 0; t < nt; ++t) {
     const float2* vt = reinterpret_cast<const float2*>(v) + (long long)t * nv * V3 * 3;
     double2* pt = reinterpret_cast<double2*>(phi) + (long long)t * np * T3;

@@ -8,12 +8,12 @@
 namespace distil {
 
 namespace {
-struct BatchRows {  // row r of [batch][rows][K]
+struct BatchRows {  // row r of [batch][rows][K], exact in double-float
   const float2* x;
   long long K;
-  __device__ __forceinline__ double2 operator()(long long r, int k) const {
+  __device__ __forceinline__ CDF operator()(long long r, int k) const {
     const float2 v = x[r * K + k];
-    return make_double2(v.x, v.y);
+    return cdf_make(df_make(v.x, 0.f), df_make(v.y, 0.f));
   }
 };
 }  // namespace
@@ -51,9 +51,7 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
   cfg.err = ctx->d_error;
   tc::Planes pa = planes_of(PA, K, M, batch, NPLA, ld);
   tc::Planes pb = planes_of(PB, K, N, batch, NPLB, ld);
-  EpiStore<float2> epi;
-  epi.out = C; epi.b_lo = 1; epi.sb_hi = (long long)M * N; epi.sb_lo = 0;
-  epi.sr = N; epi.cm = ColMap{1, 0, 0}; epi.N = N;
+  EpiStoreC64 epi{C, (long long)M * N, N, N};
   constexpr int ST = (NPLA + NPLB) > 8 ? 2 : 3;
   if (N > 64) return tc::launch_gemm<128, 32, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
   if (N > 32) return tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);

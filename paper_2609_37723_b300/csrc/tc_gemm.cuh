@@ -12,8 +12,10 @@
 // Two accumulator pairs exist so that the leading product of a fixed-point
 // split (integer-valued slices) sums exactly in its own FP32 accumulator,
 // whatever the tensor core's accumulation rounding; every scheme puts at
-// least one product into each pair.  The epilogue forms
-// D = D[0] + w1 * D[1] in FP64 and multiplies by 2^(eA[row] + eB[col] - shift).
+// least one product into each pair.  The epilogue scales both by
+// 2^(eA[row] + eB[col] - shift) (the second also by w1, all exact powers of
+// two) and hands the pair to the functor, which keeps D = D[0] + D[1] as a
+// double-float.
 //
 // One CTA computes a 128 x NT tile: warp 0 issues TMA loads into a STAGES-deep
 // ring, warp 1 allocates TMEM and issues the MMAs, warps 2..5 read the
@@ -184,16 +186,19 @@ __global__ void __launch_bounds__(192, 1)
         tmem_wait_ld();
         const int col0 = n_tile * NT + c * 16;
         if (row < cfg.M) {
-          double re[16], im[16];
+          float re0[16], re1[16], im0[16], im1[16];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int col = col0 + e;
             const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
-            const double f = ldexp(1.0, ea + eb - cfg.shift);
-            re[e] = fma((double)cfg.w1, (double)__uint_as_float(r1[e]), (double)__uint_as_float(r0[e])) * f;
-            im[e] = fma((double)cfg.w1, (double)__uint_as_float(i1[e]), (double)__uint_as_float(i0[e])) * f;
+            const float f = pow2f(ea + eb - cfg.shift);  // exact power-of-two scalings
+            const float f1 = f * cfg.w1;
+            re0[e] = __uint_as_float(r0[e]) * f;
+            im0[e] = __uint_as_float(i0[e]) * f;
+            re1[e] = __uint_as_float(r1[e]) * f1;
+            im1[e] = __uint_as_float(i1[e]) * f1;
           }
-          epi(batch, row, col0, re, im);
+          epi(batch, row, col0, re0, re1, im0, im1);
         }
       }
     }

@@ -8,7 +8,7 @@ Tolerances.  FP16x6 represents every row to 2^-31 of its largest entry
 with fixed-point slices (9 + 11 + 11 bits) whose leading products sum
 exactly in FP32, drops terms of relative size ~1e-8, and keeps FP64 between
 the contractions: 1e-6 with a wide margin (its split GEMM is checked at
-1e-7, the rounding of its complex64 output).  BF16x6 (8 + 8 + 8 bits, 2^-24): 1e-5.  BF16x3 keeps 16 bits:
+1e-7, the rounding of its complex64 output).  BF16x6 (8 + 8 + 8 bits, 2^-24): 3e-5.  BF16x3 keeps 16 bits:
 1e-3.  FP16x3 keeps 22 bits in floating pieces, but the tensor core's FP32
 accumulation is not correctly rounded: its error grows with the number of
 accumulated MMAs (measured about 2.5e-8 per step): 1e-4."""
@@ -22,7 +22,7 @@ from parity import max_c_error, max_c_scaled_error, normwise
 pytestmark = pytest.mark.gpu
 
 MODES = ["fp16x6", "bf16x6", "bf16x3", "fp16x3"]
-TOL_C = {"fp16x6": 1e-6, "fp16x3": 1e-4, "bf16x6": 1e-5, "bf16x3": 1e-3}
+TOL_C = {"fp16x6": 1e-6, "fp16x3": 1e-4, "bf16x6": 3e-5, "bf16x3": 1e-3}
 
 
 def T(x):
@@ -43,7 +43,11 @@ def test_cgemm_accuracy(cuda_lib, mode, M, N, K, batch):
     err = normwise(got, ref)
     emax = float(np.abs(got - ref).max() / np.abs(ref).max())
     print(f"cgemm {mode} M={M} N={N} K={K} b={batch}: normwise {err:.2e} max {emax:.2e}")
-    bound = {"fp16x6": 1e-7, "fp16x3": 3e-8 * max(64, K) * 6 / 16, "bf16x6": 1.5e-6, "bf16x3": 3e-4}[mode]
+    # the leading slice sums exactly; the second accumulator (about 2^-W |mid/hi|
+    # of the result) rounds inexactly, a drift linear in K (the library cuts
+    # long contractions into chunks of 4096 for that reason)
+    bound = {"fp16x6": 1e-7 + 6e-11 * K, "fp16x3": 3e-8 * max(64, K) * 6 / 16,
+             "bf16x6": 1.5e-6 + 1.5e-10 * K, "bf16x3": 3e-4}[mode]
     assert err < bound
 
 
