@@ -171,6 +171,34 @@ int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, 
                  int batch, int mode, void* workspace, size_t ws_bytes, distil_stream stream);
 
 /* ------------------------------------------------------------------ */
+/* Correlation matrix without device allocation                        */
+/* ------------------------------------------------------------------ */
+
+/* Same result as distil_correlate in the FP64 or FP32 mode, for callers that
+ * cannot allocate device memory where they need it: a process that works
+ * inside a device-memory budget reserved up front, or a latency-critical
+ * pipeline that cannot afford the device-wide synchronisation cudaMalloc /
+ * cudaFree may imply.  The call allocates nothing; its scratch is a fixed
+ * 16 MiB device array inside the library, held by every GPU that loads the
+ * library until the process exits.  (The paper has no counterpart; this is
+ * an interface convenience.)
+ *  - Arguments and layouts as distil_correlate, without workspace; mode must
+ *    be DISTIL_FP64 or DISTIL_FP32 (else DISTIL_EINVAL).
+ *  - Sizes needing more scratch than the array (FP64 about 352 N_B N_v^3
+ *    bytes: e.g. N_v = 16 with N_B <= 16, N_v = 24 with N_B <= 3) return
+ *    DISTIL_ENOMEM without touching the device.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents.
+ *    Calls that overlap on the GPU (different streams, or several host
+ *    threads) race on it: serialise them. */
+int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* phi_src,
+                             const void* tau, int nt, int nv, int np,
+                             const double* prof, int nb, int prof_per_t, int mode,
+                             void* C, distil_stream stream);
+
+/* ------------------------------------------------------------------ */
 /* Introspection                                                       */
 /* ------------------------------------------------------------------ */
 

@@ -1,0 +1,75 @@
+// distil_correlate_noalloc: the plain correlation matrix with its scratch in
+// a fixed device array instead of caller-provided workspace.
+//
+// Some callers cannot allocate device memory at the point where they need
+// the correlation matrix: a process running under a fixed device-memory
+// budget that was reserved up front, or a latency-critical pipeline that
+// cannot afford the device-wide synchronisation cudaMalloc and cudaFree may
+// imply.  This entry point calls no allocating routine at all.  Its scratch
+// is the file-scope device array below; every GPU that loads the library
+// holds it until the process exits.
+#include <mutex>
+
+#include "common.cuh"
+#include "correlate.cuh"
+
+namespace distil {
+
+// Largest scratch the entry point accepts: 16 MiB (FP64 needs about
+// 22 * 16 * N_B * N_v^3 bytes: N_v = 16 with N_B <= 16, or N_v = 24 with N_B <= 3).
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on `device` (which must be current).
+// In host code the array's name is only a host-side stand-in, so the real
+// address is looked up once per device and cached.
+static int noalloc_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) {
+    set_error("distil_correlate_noalloc: device %d out of range", device);
+    return DISTIL_EINVAL;
+  }
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("distil_correlate_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return DISTIL_ECUDA;
+    }
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return DISTIL_OK;
+}
+
+}  // namespace distil
+
+using namespace distil;
+
+extern "C" int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* phi_src, const void* tau,
+                                        int nt, int nv, int np, const double* prof, int nb, int prof_per_t,
+                                        int mode, void* C, distil_stream stream) {
+  DISTIL_CHECK_ARG(ctx != nullptr, "distil_correlate_noalloc: null context");
+  DISTIL_CHECK_ARG(mode == DISTIL_FP64 || mode == DISTIL_FP32,
+                   "distil_correlate_noalloc: mode %d not supported (FP64 or FP32 only)", mode);
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1, "distil_correlate_noalloc: nt, nv, np must be >= 1");
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_correlate_noalloc: nb=%d outside [1,16]", nb);
+  DISTIL_CHECK_ARG(tau && prof && C && ((phi_snk && phi_src) || comb3(nv) == 0),
+                   "distil_correlate_noalloc: null pointer");
+  const size_t need = correlate_plain_workspace(mode == DISTIL_FP64, nv, nb);
+  if (nv >= 3 && need > NOALLOC_SCRATCH_BYTES) {
+    set_error("distil_correlate_noalloc: N_v=%d, N_B=%d need %zu bytes of scratch, more than its %zu-byte array",
+              nv, nb, need, NOALLOC_SCRATCH_BYTES);
+    return DISTIL_ENOMEM;
+  }
+  DISTIL_CUDA(cudaSetDevice(ctx->device));
+  void* scratch = nullptr;
+  DISTIL_TRY(noalloc_scratch(ctx->device, &scratch));
+  // no context: no launch bookkeeping, nothing allocated on the host either
+  return correlate_plain(nullptr, mode == DISTIL_FP64, phi_snk, phi_src, tau, nt, nv, np, prof, nb, prof_per_t, C,
+                         scratch, NOALLOC_SCRATCH_BYTES, reinterpret_cast<cudaStream_t>(stream));
+}

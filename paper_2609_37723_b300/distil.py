@@ -33,7 +33,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOT
 EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_elementals_workspace", "distil_elementals",
            "distil_correlate_workspace", "distil_correlate", "distil_gevp",
-           "distil_cgemm_workspace", "distil_cgemm",
+           "distil_cgemm_workspace", "distil_cgemm", "distil_correlate_noalloc",
            "distil_mode_supported", "distil_profile_enable", "distil_profile_read"]
 
 _lib = None
@@ -76,6 +76,9 @@ def _declare(L):
     L.distil_cgemm.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int,
                                c_void_p, c_size_t, c_void_p]
     L.distil_cgemm.restype = c_int
+    L.distil_correlate_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                           c_int, c_int, c_int, c_void_p, c_void_p]
+    L.distil_correlate_noalloc.restype = c_int
     L.distil_mode_supported.argtypes = [c_int]
     L.distil_mode_supported.restype = c_int
     L.distil_profile_enable.argtypes = [c_void_p, c_int]
