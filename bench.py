@@ -67,6 +67,8 @@ def make_inputs(cid: int, cfg: int, workers: int):
         import multiprocessing as mp
         from multiprocessing import shared_memory
         shm = shared_memory.SharedMemory(create=True, size=int(np.prod(shape)) * dtype.itemsize)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"   # one BLAS thread per worker process (inherited at spawn)
         try:
             chunks = [list(range(w, p.nt, workers)) for w in range(workers)]
             with mp.get_context("spawn").Pool(workers) as pool:

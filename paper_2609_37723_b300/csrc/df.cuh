@@ -43,6 +43,17 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   s.lo = __fadd_rn(s.lo, t.lo);
   return quick_two_sum(s.hi, s.lo);
 }
+// a1 b1 + a2 b2 + a3 b3 + a4 b4 as a double-float: exact products, the
+// leading parts summed by TwoSum, the rounding terms added in FP32 (their
+// own error is of order 2^-48 of the largest product).
+__device__ __forceinline__ DF dot4(float a1, float b1, float a2, float b2, float a3, float b3, float a4, float b4) {
+  const float p1 = a1 * b1, p2 = a2 * b2, p3 = a3 * b3, p4 = a4 * b4;
+  const float e1 = fmaf(a1, b1, -p1), e2 = fmaf(a2, b2, -p2), e3 = fmaf(a3, b3, -p3), e4 = fmaf(a4, b4, -p4);
+  const DF s12 = two_sum(p1, p2), s34 = two_sum(p3, p4);
+  const DF s = two_sum(s12.hi, s34.hi);
+  const float lo = ((e1 + e2) + (e3 + e4)) + (s12.lo + s34.lo) + s.lo;
+  return quick_two_sum(s.hi, lo);
+}
 __device__ __forceinline__ DF df_neg(DF a) { return df_make(-a.hi, -a.lo); }
 __device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ DF df_mul(DF a, DF b) {

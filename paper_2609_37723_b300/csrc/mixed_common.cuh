@@ -119,7 +119,7 @@ __device__ __forceinline__ void make_pieces(DF x, int e, int H, typename tc::Pie
 // and exps[r]; optionally the row's 2-norm (with a small safety margin)
 // into norms[r].  One warp per row: pass 1 finds max |re|, |im| over the
 // row, pass 2 writes the pieces.  Src::operator()(r, k) returns the element
-// as a complex double-float.
+// as a complex double-float, Src::approx(r, k) an FP32 estimate of it.
 template <bool BF16, bool FIXED, int NPC, class Src>
 __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, long long rows_per, int K, int H,
                                                          typename tc::Piece<BF16>::T* __restrict__ out, long long ld,
@@ -130,16 +130,16 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   if (r >= nrows) return;
   float m = 0.f, ss = 0.f;
   for (int k = lane; k < K; k += 32) {
-    const CDF v = src(r, k);
-    m = fmaxf(m, fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
-    ss = fmaf(v.re.hi, v.re.hi, fmaf(v.im.hi, v.im.hi, ss));
+    const float2 v = src.approx(r, k);  // FP32 estimate: enough for the exponent and the norm
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
   }
   for (int o = 16; o > 0; o >>= 1) {
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     ss += __shfl_xor_sync(0xffffffffu, ss, o);
   }
-  // a rounded hi part may sit just below the true magnitude: pad by 2^-20
-  const int e = row_exponent(m * (1.f + 1.f / 1048576.f));
+  // the FP32 estimate may sit slightly below the true magnitude: pad by 2^-16
+  const int e = row_exponent(m * (1.f + 1.f / 65536.f));
   if (lane == 0) {
     exps[r] = e;
     if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
@@ -160,19 +160,79 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   }
 }
 
+// Long rows (K <= 512 PER): one block of 512 threads per row, each thread
+// holding PER elements in registers, so every element is formed once and
+// the exponent comes from the exact maximum.
+template <bool BF16, bool FIXED, int NPC, int PER, class Src>
+__global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, long long rows_per, int K, int H,
+                                                                typename tc::Piece<BF16>::T* __restrict__ out,
+                                                                long long ld, int* __restrict__ exps,
+                                                                float* __restrict__ norms) {
+  using P16 = typename tc::Piece<BF16>::T;
+  __shared__ float red_m[16], red_s[16];
+  __shared__ int sh_e;
+  const long long r = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  CDF v[PER];
+  float m = 0.f, ss = 0.f;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int k = threadIdx.x + 512 * u;
+    v[u] = k < K ? src(r, k) : cdf_zero();
+    m = fmaxf(m, fmaxf(fabsf(v[u].re.hi), fabsf(v[u].im.hi)));
+    ss = fmaf(v[u].re.hi, v[u].re.hi, fmaf(v[u].im.hi, v[u].im.hi, ss));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if (lane == 0) { red_m[wid] = m; red_s[wid] = ss; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 16; ++w) { m = fmaxf(m, red_m[w]); ss += red_s[w]; }
+    sh_e = row_exponent(m * (1.f + 1.f / 65536.f));
+    exps[r] = sh_e;
+    if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
+  }
+  __syncthreads();
+  const int e = sh_e;
+  const long long coord = r / rows_per, rr = r % rows_per;
+  const long long ps = rows_per * ld;
+  P16* base = out + coord * (2 * NPC) * ps + rr * ld;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int k = threadIdx.x + 512 * u;
+    if (k >= K) break;
+    P16 pr[NPC], pi[NPC];
+    make_pieces<BF16, FIXED, NPC>(v[u].re, e, H, pr);
+    make_pieces<BF16, FIXED, NPC>(v[u].im, e, H, pi);
+#pragma unroll
+    for (int i = 0; i < NPC; ++i) {
+      base[(2 * i) * ps + k] = pr[i];
+      base[(2 * i + 1) * ps + k] = pi[i];
+    }
+  }
+}
+
 // Planes descriptor matching split_rows_kernel's layout.
 inline tc::Planes planes_of(void* base, long long K, long long rows_per, long long ncoord, int npl, long long ld) {
   return tc::Planes{base, K, rows_per, npl, ncoord, ld, rows_per * ld, (long long)npl * rows_per * ld};
 }
 
 template <bool BF16, bool FIXED, int NPC, class Src>
-inline int split_rows(distil_ctx* ctx, const Src& src, long long nrows, long long rows_per, int K, int H, void* out,
-                      long long ld, int* exps, cudaStream_t s, float* norms = nullptr) {
+inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long long nrows, long long rows_per, int K,
+                      int H, void* out, long long ld, int* exps, cudaStream_t s, float* norms = nullptr) {
   if (nrows <= 0) return DISTIL_OK;
   const long long threads = nrows * 32;
-  Launch L(ctx, "split_rows", s);
-  split_rows_kernel<BF16, FIXED, NPC, Src><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-      src, nrows, rows_per, K, H, reinterpret_cast<typename tc::Piece<BF16>::T*>(out), ld, exps, norms);
+  Launch L(ctx, name, s);
+  auto* o16 = reinterpret_cast<typename tc::Piece<BF16>::T*>(out);
+  if (K > 2048 && K <= 4096)
+    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src><<<(unsigned)nrows, 512, 0, s>>>(src, rows_per, K, H, o16, ld, exps, norms);
+  else if (K > 1024 && K <= 2048)
+    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src><<<(unsigned)nrows, 512, 0, s>>>(src, rows_per, K, H, o16, ld, exps, norms);
+  else
+    split_rows_kernel<BF16, FIXED, NPC, Src><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        src, nrows, rows_per, K, H, reinterpret_cast<typename tc::Piece<BF16>::T*>(out), ld, exps, norms);
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
 }

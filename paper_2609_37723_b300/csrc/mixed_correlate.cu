@@ -98,6 +98,10 @@ struct AaSrc {  // rows (a'*4 + beta)*n + i', K = i
     const float s = (beta & 1) ? -tc::pow2f(-etau[0]) : tc::pow2f(-etau[0]);
     return cdf_of(tau[((long long)alpha * n + i) * 4 * n + ap * n + ip], s);
   }
+  __device__ __forceinline__ float2 approx(long long r, int i) const {
+    const CDF v = (*this)(r, i);
+    return make_float2(v.re.hi, v.im.hi);
+  }
 };
 struct TTSrc {  // rows (b'j'), K = (beta j): tau^T
   const float2* tau;
@@ -105,6 +109,11 @@ struct TTSrc {  // rows (b'j'), K = (beta j): tau^T
   int n;
   __device__ __forceinline__ CDF operator()(long long r, int k) const {
     return cdf_of(tau[(long long)k * 4 * n + r], tc::pow2f(-etau[0]));
+  }
+  __device__ __forceinline__ float2 approx(long long r, int k) const {
+    const float2 x = tau[(long long)k * 4 * n + r];
+    const float s = tc::pow2f(-etau[0]);
+    return make_float2(x.x * s, x.y * s);
   }
 };
 struct TcSrc {  // rows c*n + k, K = k': T^c[k][k']
@@ -122,6 +131,10 @@ struct TcSrc {  // rows c*n + k, K = k': T^c[k][k']
     const int mu = (c <= 2) ? 0 : 1;
     const int gp = (c == 1 || c == 3) ? 2 : 3;
     return cdf_of(tau[((long long)mu * n + k) * n4 + gp * n + kp], s);
+  }
+  __device__ __forceinline__ float2 approx(long long r, int kp) const {
+    const CDF v = (*this)(r, kp);
+    return make_float2(v.re.hi, v.im.hi);
   }
 };
 // sorted-triple lookup with sign; 0 on a repeated index
@@ -145,6 +158,20 @@ struct GSrc {  // rows a*n^2 + k*n + j, K = i: g_i g_j g_k Phi_ijk
     const DF* ga = g + (long long)a * n;
     return phi_at(phi, i, j, k, df_mul(df_mul(ga[i], ga[j]), ga[k]));
   }
+  __device__ __forceinline__ float2 approx(long long r, int i) const {
+    const long long n2 = (long long)n * n;
+    const int a = (int)(r / n2);
+    const int k = (int)((r % n2) / n), j = (int)(r % n);
+    if (i == j || j == k || i == k) return make_float2(0.f, 0.f);
+    int x = i, y = j, z = k;
+    if (x > y) { int t = x; x = y; y = t; }
+    if (y > z) { int t = y; y = z; z = t; }
+    if (x > y) { int t = x; x = y; y = t; }
+    const DF* ga = g + (long long)a * n;
+    const float w = ga[i].hi * ga[j].hi * ga[k].hi;
+    const CDF p = phi[triple_rank(x, y, z)];
+    return make_float2(p.re.hi * w, p.im.hi * w);
+  }
 };
 struct SSrc {  // rows b*P2 + pair(i'<j'), K = k': g g g conj(Phi_{i'j'k'})
   const CDF* phi;
@@ -157,6 +184,19 @@ struct SSrc {  // rows b*P2 + pair(i'<j'), K = k': g g g conj(Phi_{i'j'k'})
     pair_unrank(r % P2, ip, jp);
     const DF* gb = g + (long long)b * n;
     return cdf_conj(phi_at(phi, ip, jp, kp, df_mul(df_mul(gb[ip], gb[jp]), gb[kp])));
+  }
+  __device__ __forceinline__ float2 approx(long long r, int kp) const {
+    const int b = (int)(r / P2);
+    int ip, jp;
+    pair_unrank(r % P2, ip, jp);
+    if (kp == ip || kp == jp) return make_float2(0.f, 0.f);
+    int x = ip, y = jp, z = kp;
+    if (y > z) { int t = y; y = z; z = t; }
+    if (x > y) { int t = x; x = y; y = t; }
+    const DF* gb = g + (long long)b * n;
+    const float w = gb[ip].hi * gb[jp].hi * gb[kp].hi;
+    const CDF p = phi[triple_rank(x, y, z)];
+    return make_float2(p.re.hi * w, p.im.hi * w);
   }
 };
 
@@ -188,10 +228,42 @@ struct EpiSplitU {
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
   __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
+    using P16 = typename tc::Piece<BF16>::T;
     const long long n2 = (long long)n * n;
     const int aa = batch >> 2, beta = batch & 3;  // aa = a*3 + a'
     const long long ps = n2 * ld4;
     auto* base = out + (long long)aa * (2 * NPC) * ps;
+    if ((n & 15) == 0 && col0 + 16 <= (int)n2) {
+      // the 16 columns share k and run over 16 consecutive j: assemble each
+      // plane's 16 pieces in registers and write them as two 16-byte stores
+      const int k = col0 / n, j0 = col0 % n;
+      const long long ur = (long long)row * n + k;
+      const int ex = eU[(long long)aa * n2 + ur];
+      uint32_t w[2 * NPC][8];
+#pragma unroll
+      for (int e = 0; e < 16; e += 2) {
+        P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
+        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), ex, H, pr0);
+        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), ex, H, pi0);
+        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), ex, H, pr1);
+        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), ex, H, pi1);
+#pragma unroll
+        for (int q = 0; q < NPC; ++q) {
+          w[2 * q][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pr0[q]) |
+                            ((uint32_t)reinterpret_cast<const uint16_t&>(pr1[q]) << 16);
+          w[2 * q + 1][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pi0[q]) |
+                                ((uint32_t)reinterpret_cast<const uint16_t&>(pi1[q]) << 16);
+        }
+      }
+      P16* d = base + ur * ld4 + (long long)beta * n + j0;
+#pragma unroll
+      for (int pl = 0; pl < 2 * NPC; ++pl) {
+        uint4* d4 = reinterpret_cast<uint4*>(d + pl * ps);
+        d4[0] = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+        d4[1] = make_uint4(w[pl][4], w[pl][5], w[pl][6], w[pl][7]);
+      }
+      return;
+    }
 #pragma unroll 4
     for (int e = 0; e < 16; ++e) {
       const int c = col0 + e;
@@ -369,11 +441,11 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
   }
   // ---- split operands (one warp per row, per-row exponents)
   const int H = sch.H;
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, AaSrc{tau, etau, nv}, 12 * n, n, nv, H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TTSrc{tau, etau, nv}, 4 * n, 4 * n, 4 * nv, H, w.TT, w.ld4, w.eTT, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, TcSrc{tau, etau, nv}, 5 * n, n, nv, H, w.Tc, w.ldn, w.eTc, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, GSrc{w.phs, g_snk, nv}, nb * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, SSrc{w.ph0, g_src, nv, P2}, nb * P2, P2, nv, H, w.S, w.ldn, w.eS, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_tau", AaSrc{tau, etau, nv}, 12 * n, n, nv, H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TTSrc{tau, etau, nv}, 4 * n, 4 * n, 4 * nv, H, w.TT, w.ld4, w.eTT, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcSrc{tau, etau, nv}, 5 * n, n, nv, H, w.Tc, w.ldn, w.eTc, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_sink", GSrc{w.phs, g_snk, nv}, nb * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_source", SSrc{w.ph0, g_src, nv, P2}, nb * P2, P2, nv, H, w.S, w.ldn, w.eS, s)));
   {
     Launch L(ctx, "u_exponent", s);
     u_exponent_kernel<<<nblk(3 * nb * n2), 256, 0, s>>>(w.nAa, w.nG, nv, nb, w.eU);

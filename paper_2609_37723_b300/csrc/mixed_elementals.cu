@@ -54,49 +54,58 @@ struct MomArgs {
   int mom[EL_MAX_MOM][3];
 };
 
-// a*b - c*d for complex FP32 inputs, exactly products then double-float sums
-__device__ __forceinline__ DF dot2_sub(float a, float b, float c, float d) {
-  return df_sub(two_prod(a, b), two_prod(c, d));
-}
-struct WSrc {  // rows q (pairs), K = (x, a) from K0
+struct WSrc {  // rows q (pairs), K = (x, a) from K0 (3 V3 < 2^31)
   const float2* v;  // v[t] = [n][V3][3]
   const int2* pairs;
   long long V3;
-  long long K0;
+  int K0;
   __device__ __forceinline__ CDF operator()(long long q, int kk) const {
-    const long long K = K0 + kk;
-    const long long x = K / 3;
-    const int a = (int)(K % 3), b = (a + 1) % 3, c = (a + 2) % 3;
+    const int K = K0 + kk;
+    const int x = K / 3, a = K - 3 * x;
+    const int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
     const int2 jk = pairs[q];
     const float2* vj = v + ((long long)jk.x * V3 + x) * 3;
     const float2* vk = v + ((long long)jk.y * V3 + x) * 3;
     const float2 jb = vj[b], jc = vj[c], kb = vk[b], kc = vk[c];
     // w^a = v_j^b v_k^c - v_j^c v_k^b
-    const DF re = df_sub(dot2_sub(jb.x, kc.x, jb.y, kc.y), dot2_sub(jc.x, kb.x, jc.y, kb.y));
-    const DF im = df_sub(df_add(two_prod(jb.x, kc.y), two_prod(jb.y, kc.x)),
-                         df_add(two_prod(jc.x, kb.y), two_prod(jc.y, kb.x)));
+    const DF re = dot4(jb.x, kc.x, -jb.y, kc.y, -jc.x, kb.x, jc.y, kb.y);
+    const DF im = dot4(jb.x, kc.y, jb.y, kc.x, -jc.x, kb.y, -jc.y, kb.x);
     return cdf_make(re, im);
+  }
+  __device__ __forceinline__ float2 approx(long long q, int kk) const {
+    const int K = K0 + kk;
+    const int x = K / 3, a = K - 3 * x;
+    const int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+    const int2 jk = pairs[q];
+    const float2* vj = v + ((long long)jk.x * V3 + x) * 3;
+    const float2* vk = v + ((long long)jk.y * V3 + x) * 3;
+    const float2 jb = vj[b], jc = vj[c], kb = vk[b], kc = vk[c];
+    return make_float2(jb.x * kc.x - jb.y * kc.y - (jc.x * kb.x - jc.y * kb.y),
+                       jb.x * kc.y + jb.y * kc.x - (jc.x * kb.y + jc.y * kb.x));
   }
 };
 
-struct ESrc {  // rows i*np + q, K = (x, a) from K0
+struct ESrc {  // rows i*np + q, K = (x, a) from K0 (3 V3 < 2^31)
   const float2* v;
   const CDF* tab;
   MomArgs m;
   long long V3;
-  long long K0;
+  int K0;
   __device__ __forceinline__ CDF operator()(long long r, int kk) const {
-    const long long K = K0 + kk;
-    const long long x = K / 3;
-    const int a = (int)(K % 3);
-    const int i = (int)(r / m.np), q = (int)(r % m.np);
+    const int K = K0 + kk;
+    const int x = K / 3, a = K - 3 * x;
+    const int i = (int)r / m.np, q = (int)r - i * m.np;
     const int L = m.L;
-    const int xs = (int)(x % L), ys = (int)((x / L) % L), zs = (int)(x / ((long long)L * L));
+    const int xy = x / L, xs = x - xy * L, zs = xy / L, ys = xy - zs * L;
     const int ph = (m.mom[q][0] * xs + m.mom[q][1] * ys + m.mom[q][2] * zs) % L;
     const CDF e = tab[ph];
     const float2 u = v[((long long)i * V3 + x) * 3 + a];
     // (e.re + i e.im)(u.x + i u.y)
     return cdf_make(df_sub(df_mul_f(e.re, u.x), df_mul_f(e.im, u.y)), df_add(df_mul_f(e.re, u.y), df_mul_f(e.im, u.x)));
+  }
+  __device__ __forceinline__ float2 approx(long long r, int kk) const {
+    const CDF z = (*this)(r, kk);
+    return make_float2(z.re.hi, z.im.hi);
   }
 };
 
@@ -186,8 +195,8 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
   cfg.err = ctx->d_error;
   for (long long K0 = 0; K0 < Ktot; K0 += EL_KC) {
     const int Kc = (int)((Ktot - K0) < EL_KC ? (Ktot - K0) : EL_KC);
-    DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, WSrc{vt, w.pairs, V3, K0}, P2, P2, Kc, H, w.W, w.ldk, w.eW, s)));
-    DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, ESrc{vt, w.tab, mom, V3, K0}, R, R, Kc, H, w.E, w.ldk, w.eE, s)));
+    DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_pairs", WSrc{vt, w.pairs, V3, (int)K0}, P2, P2, Kc, H, w.W, w.ldk, w.eW, s)));
+    DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_phase", ESrc{vt, w.tab, mom, V3, (int)K0}, R, R, Kc, H, w.E, w.ldk, w.eE, s)));
     Planes A = planes_of(w.W, Kc, P2, 1, NPLA, w.ldk);
     Planes B = planes_of(w.E, Kc, R, 1, NPLB, w.ldk);
     cfg.M = (int)P2; cfg.N = (int)R; cfg.K = Kc;

@@ -15,6 +15,7 @@ struct BatchRows {  // row r of [batch][rows][K], exact in double-float
     const float2 v = x[r * K + k];
     return cdf_make(df_make(v.x, 0.f), df_make(v.y, 0.f));
   }
+  __device__ __forceinline__ float2 approx(long long r, int k) const { return x[r * K + k]; }
 };
 }  // namespace
 
@@ -41,8 +42,8 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
     set_error("distil_cgemm: workspace too small");
     return DISTIL_ENOMEM;
   }
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, BatchRows{A, K}, (long long)batch * M, M, K, sch.H, PA, ld, eA, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, BatchRows{B, K}, (long long)batch * N, N, K, sch.H, PB, ld, eB, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_cgemm", BatchRows{A, K}, (long long)batch * M, M, K, sch.H, PA, ld, eA, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_cgemm", BatchRows{B, K}, (long long)batch * N, N, K, sch.H, PB, ld, eB, s)));
   tc::GemmCfg cfg{};
   fill_products(cfg, sch);
   cfg.M = M; cfg.N = N; cfg.K = K;

@@ -18,7 +18,8 @@
 // double-float.
 //
 // One CTA computes a 128 x NT tile: warp 0 issues TMA loads into a STAGES-deep
-// ring, warp 1 allocates TMEM and issues the MMAs, warps 2..5 read the
+// ring, warp 1 allocates TMEM and issues the MMAs, and 8 epilogue warps (two
+// per TMEM lane quarter, each owning half of the columns) read the
 // accumulators back (tcgen05.ld) and hand 16-column slices to the epilogue
 // functor.  All waits are bounded (tc.cuh).
 #pragma once
@@ -63,8 +64,10 @@ constexpr size_t gemm_smem_bytes() {
   return (size_t)STAGES * TileGeom<NT, KC, NPLA, NPLB>::STAGE + 1024 /*align*/ + 256 /*barriers*/;
 }
 
+constexpr int TC_THREADS = 64 + 8 * 32;  // producer, MMA issuer, 8 epilogue warps
+
 template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    GemmCfg cfg, Epi epi) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
@@ -168,7 +171,8 @@ __global__ void __launch_bounds__(192, 1)
     mma_commit(accf);  // fires once every MMA above has completed (also on abort)
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;             // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;   // which half of the NT columns
     bool ok = mbar_wait(accf, 0, cfg.err, TC_ERR_ACC_WAIT);
     ok = __all_sync(0xffffffffu, ok && !*(volatile uint32_t*)abort_flag);  // warp-uniform for tcgen05.ld
     tc_fence_after();
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
       const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = 0; c < NT / 16; ++c) {
+      for (int c = half * (NT / 32); c < (half + 1) * (NT / 32); ++c) {
         uint32_t r0[16], i0[16], r1[16], i1[16];
         tmem_ld16(tl + c * 16, r0);
         tmem_ld16(tl + NT + c * 16, i0);

@@ -48,7 +48,7 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
   }
   {
     Launch L(ctx, name, s);
-    kern<<<grid, 192, smem, s>>>(ma, mb, cfg, epi);
+    kern<<<grid, TC_THREADS, smem, s>>>(ma, mb, cfg, epi);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
