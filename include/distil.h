@@ -202,6 +202,17 @@ int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* p
 /* Introspection                                                       */
 /* ------------------------------------------------------------------ */
 
+/* Device-side status of ctx.  Kernels record in a device word the first
+ * bounded wait that expired (a tensor-core pipeline stage that never
+ * arrived); once set, later tensor-core launches of ctx return at once and
+ * leave their outputs unwritten.  This call synchronises the device, stores
+ * the code in *code (0 = no expired wait; 1 = MMA waiting for a TMA stage,
+ * 2 = TMA producer waiting for a free stage, 3 = epilogue waiting for the
+ * accumulator, 4 = teardown waiting for copies in flight) and returns
+ * DISTIL_ETIMEOUT with a message when it is nonzero.  reset != 0 clears
+ * the word afterwards.  code may be NULL. */
+int distil_device_status(distil_ctx* ctx, int reset, unsigned* code);
+
 /* 1 if this build implements `mode`, else 0 (no device needed). */
 int distil_mode_supported(int mode);
 

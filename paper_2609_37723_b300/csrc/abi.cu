@@ -184,6 +184,23 @@ int distil_mode_supported(int mode) {
   return is_mixed(mode) ? mixed_mode_built(mode) : 1;
 }
 
+int distil_device_status(distil_ctx* ctx, int reset, unsigned* code) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CUDA(cudaDeviceSynchronize());
+  unsigned w = 0;
+  DISTIL_CUDA(cudaMemcpy(&w, ctx->d_error, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (code) *code = w;
+  if (reset) DISTIL_CUDA(cudaMemset(ctx->d_error, 0, sizeof(unsigned)));
+  if (w) {
+    static const char* what[] = {"", "MMA waiting for a TMA stage", "TMA producer waiting for a free stage",
+                                 "epilogue waiting for the accumulator", "teardown waiting for copies in flight"};
+    set_error("a bounded device wait expired: %s (code %u)", w < 5 ? what[w] : "unknown", w);
+    return DISTIL_ETIMEOUT;
+  }
+  return DISTIL_OK;
+}
+
 int distil_profile_enable(distil_ctx* ctx, int timing) {
   g_err[0] = 0;
   DISTIL_TRY(enter(ctx));

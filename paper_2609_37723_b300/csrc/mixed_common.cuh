@@ -253,7 +253,7 @@ struct ColMap {
 // (leading-slice part, cross-term part): D = re0 + re1, im0 + im1.
 
 // out[batch][row * sr + colmap(col)] = D as a complex double-float.
-struct EpiStoreCDF {
+struct EpiStoreCDF : tc::EpiStateless {
   CDF* out;
   long long sb_hi, sb_lo;
   int b_lo;
@@ -261,7 +261,7 @@ struct EpiStoreCDF {
   ColMap cm;
   int N;
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
+  __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     CDF* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
 #pragma unroll
@@ -274,13 +274,13 @@ struct EpiStoreCDF {
 };
 
 // out[batch][row][col] = D rounded to complex64 (public split GEMM).
-struct EpiStoreC64 {
+struct EpiStoreC64 : tc::EpiStateless {
   float2* out;
   long long sb;
   long long sr;
   int N;
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
+  __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     float2* base = out + (long long)batch * sb + (long long)row * sr;
 #pragma unroll

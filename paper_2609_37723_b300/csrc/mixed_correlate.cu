@@ -220,13 +220,13 @@ __global__ void u_exponent_kernel(const float* __restrict__ nAa, const float* __
 // Step i epilogue: split U straight from the accumulator pair into the
 // A-operand pieces of step j, U[(a,a')][plane][(i',k)][(beta,j)].
 template <bool BF16, bool FIXED, int NPC>
-struct EpiSplitU {
+struct EpiSplitU : tc::EpiStateless {
   typename tc::Piece<BF16>::T* out;
   const int* eU;
   int n, H;
   long long ld4;
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
-  __device__ __forceinline__ void operator()(int batch, int row, int col0, const float* re0, const float* re1,
+  __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     using P16 = typename tc::Piece<BF16>::T;
     const long long n2 = (long long)n * n;
@@ -264,7 +264,7 @@ struct EpiSplitU {
       }
       return;
     }
-#pragma unroll 4
+#pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int c = col0 + e;
       if (c >= (int)n2) break;
@@ -293,14 +293,23 @@ __device__ __forceinline__ void df_acc_prod(float& s, float& c, DF a, DF b) {
   c += t.lo + __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
 }
 
-// C[q][a][b][t] += 2^scale sum_terms coef sum_{i'<j',k} (V^a_{i'j'k} - V^a_{j'i'k}) X^{b,c}_{pair,k}
-// V[a][slot][j'][i'][k], X[b][c][pair][k] (double-floats); block = (a, chunk of pairs).
+// C[q][a][b][t] += 2^scale sum_terms coef sum_{i'<j',k} (V^a_{j'i'k} - V^a_{i'j'k}) X^{b,c}_{pair,k}
+// V[a][slot][j'][i'][k], X[b][c][pair][k] (double-floats).  Warp w of a
+// block takes a = w and 32 consecutive (pair, k) elements per iteration, so
+// the nb warps of a block read the same X values and all but the first find
+// them in L1: X leaves HBM once per launch.  The two terms that share a
+// source matrix are summed before the product.
+__device__ __forceinline__ CDF ldg_cdf(const CDF* p) {  // p is 16-byte aligned
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return cdf_make(df_make(v.x, v.y), df_make(v.z, v.w));
+}
 template <int MAXB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * MAXB)
 dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int nb, const int* __restrict__ etau,
               const int* __restrict__ esnk, const int* __restrict__ esrc, Cx<double>* __restrict__ C,
               long long cstride_a, long long cstride_b) {
-  const int a = blockIdx.y;
+  const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (a >= nb) return;
   const long long P2 = comb2(nv);
   const long long n3 = (long long)nv * nv * nv;
   const long long work = P2 * nv;
@@ -308,59 +317,51 @@ dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int 
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) sr[b] = cr[b] = si[b] = ci[b] = 0.f;
   const CDF* Va = V + (long long)a * NPAIR * n3;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < work;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = blockIdx.x * 32LL + lane; e < work; e += (long long)gridDim.x * 32) {
     const long long q = e / nv;
-    const int k = (int)(e % nv);
+    const int k = (int)(e - q * nv);
     int ip, jp;
     pair_unrank(q, ip, jp);
-    CDF w[NTERM];
+    const long long o1 = ((long long)jp * nv + ip) * nv + k, o2 = ((long long)ip * nv + jp) * nv + k;
+    CDF w[NSRC];
+#pragma unroll
+    for (int c = 0; c < NSRC; ++c) w[c] = cdf_zero();
 #pragma unroll
     for (int t = 0; t < NTERM; ++t) {
       const CDF* Vs = Va + dot_slot(t) * n3;
-      const CDF d = cdf_sub(Vs[((long long)jp * nv + ip) * nv + k], Vs[((long long)ip * nv + jp) * nv + k]);
+      const CDF d = cdf_sub(ldg_cdf(Vs + o1), ldg_cdf(Vs + o2));
       const float cf = (float)dot_coef(t);
-      w[t] = cdf_make(df_mul_f(d.re, cf), df_mul_f(d.im, cf));
+      const CDF wt = cdf_make(df_mul_f(d.re, cf), df_mul_f(d.im, cf));
+      w[dot_src(t)] = cdf_add(w[dot_src(t)], wt);
     }
 #pragma unroll
     for (int b = 0; b < MAXB; ++b) {
       if (b >= nb) break;
-      const CDF* Xb = X + (long long)b * NSRC * work;
+      const CDF* Xb = X + (long long)b * NSRC * work + e;
 #pragma unroll
-      for (int t = 0; t < NTERM; ++t) {
-        const CDF x = Xb[dot_src(t) * work + e];
-        df_acc_prod(sr[b], cr[b], w[t].re, x.re);
-        df_acc_prod(sr[b], cr[b], df_neg(w[t].im), x.im);
-        df_acc_prod(si[b], ci[b], w[t].re, x.im);
-        df_acc_prod(si[b], ci[b], w[t].im, x.re);
+      for (int c = 0; c < NSRC; ++c) {
+        const CDF x = ldg_cdf(Xb + c * work);
+        df_acc_prod(sr[b], cr[b], w[c].re, x.re);
+        df_acc_prod(sr[b], cr[b], df_neg(w[c].im), x.im);
+        df_acc_prod(si[b], ci[b], w[c].re, x.im);
+        df_acc_prod(si[b], ci[b], w[c].im, x.re);
       }
     }
   }
-  __shared__ double red[2][8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double scale = ldexp(1.0, 3 * etau[0] + esnk[0] + esrc[0]);
-  for (int b = 0; b < nb && b < MAXB; ++b) {
+#pragma unroll
+  for (int b = 0; b < MAXB; ++b) {
+    if (b >= nb) break;
     DF vr = two_sum(sr[b], cr[b]), vi = two_sum(si[b], ci[b]);
     for (int o = 16; o > 0; o >>= 1) {
       vr = df_add(vr, df_make(__shfl_xor_sync(0xffffffffu, vr.hi, o), __shfl_xor_sync(0xffffffffu, vr.lo, o)));
       vi = df_add(vi, df_make(__shfl_xor_sync(0xffffffffu, vi.hi, o), __shfl_xor_sync(0xffffffffu, vi.lo, o)));
     }
     if (lane == 0) {
-      red[0][wid] = df_to_double(vr);
-      red[1][wid] = df_to_double(vi);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double zr = 0.0, zi = 0.0;
-      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) {
-        zr += red[0][u];
-        zi += red[1][u];
-      }
       double* dst = reinterpret_cast<double*>(C + a * cstride_a + b * cstride_b);
-      atomicAdd(dst, zr * scale);
-      atomicAdd(dst + 1, zi * scale);
+      atomicAdd(dst, df_to_double(vr) * scale);
+      atomicAdd(dst + 1, df_to_double(vi) * scale);
     }
-    __syncthreads();
   }
 }
 
@@ -463,8 +464,21 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     cfg.M = nv; cfg.N = (int)n2; cfg.K = nv;
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
     cfg.b = tc::OpMap{12, nb, 1, 0, 0, (int)n2, w.eG};
-    EpiSplitU<BF16, FIXED, NA> epi{(P16*)w.U, w.eU, nv, H, w.ld4};
+    EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
     DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
+  }
+  // ---- source: batch (b, c) = nb x 5; X[b][c][pair][k]
+  {
+    Planes A = planes_of(w.S, n, P2, nb, NPLA, w.ldn);
+    Planes B = planes_of(w.Tc, n, n, NSRC, NPLB, w.ldn);
+    cfg.M = (int)P2; cfg.N = nv; cfg.K = nv;
+    cfg.a = tc::OpMap{NSRC, nb, 1, 0, 0, (int)P2, w.eS};
+    cfg.b = tc::OpMap{1, NSRC, 1, 0, 0, nv, w.eTc};
+    EpiStoreCDF epi;
+    epi.out = w.X;
+    epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
+    epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
   }
   // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
@@ -480,26 +494,16 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
     DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
   }
-  // ---- source: batch (b, c) = nb x 5; X[b][c][pair][k]
-  {
-    Planes A = planes_of(w.S, n, P2, nb, NPLA, w.ldn);
-    Planes B = planes_of(w.Tc, n, n, NSRC, NPLB, w.ldn);
-    cfg.M = (int)P2; cfg.N = nv; cfg.K = nv;
-    cfg.a = tc::OpMap{NSRC, nb, 1, 0, 0, (int)P2, w.eS};
-    cfg.b = tc::OpMap{1, NSRC, 1, 0, 0, nv, w.eTc};
-    EpiStoreCDF epi;
-    epi.out = w.X;
-    epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
-    epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
-  }
   // ---- dot
   {
-    long long work = P2 * n;
-    unsigned gx = nblk(work);
-    if (gx > 592) gx = 592;
+    const long long work = P2 * n;
+    unsigned gx = (unsigned)((work + 31) / 32);
+    if (gx > 1184) gx = 1184;
     Launch L(ctx, "dot", s);
-    dot_df_kernel<16><<<dim3(gx, nb), 256, 0, s>>>(w.V, w.X, nv, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
+    if (nb <= 8)
+      dot_df_kernel<8><<<gx, 32 * 8, 0, s>>>(w.V, w.X, nv, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
+    else
+      dot_df_kernel<16><<<gx, 32 * 16, 0, s>>>(w.V, w.X, nv, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;

@@ -111,7 +111,7 @@ struct ESrc {  // rows i*np + q, K = (x, a) from K0 (3 V3 < 2^31)
 
 // Phi_acc[q][r] (+)= D for the pair rows q and (i, q') columns r; the first
 // chunk stores.  Tiles with min i >= max j hold no kept output.
-struct EpiPhiAcc {
+struct EpiPhiAcc : tc::EpiStateless {
   CDF* acc;
   const int2* pairs;
   long long P2;
@@ -123,7 +123,7 @@ struct EpiPhiAcc {
     const int imin = (n_tile * nt) / np;   // rows are i * np + q
     return imin >= jmax;
   }
-  __device__ __forceinline__ void operator()(int, int row, int col0, const float* re0, const float* re1,
+  __device__ __forceinline__ void operator()(State&, int, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     CDF* dst = acc + (long long)row * N + col0;
 #pragma unroll
@@ -202,11 +202,13 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
     cfg.M = (int)P2; cfg.N = (int)R; cfg.K = Kc;
     cfg.a = tc::OpMap{1, 1, 0, 0, 0, (int)P2, w.eW};
     cfg.b = tc::OpMap{1, 1, 0, 0, 0, (int)R, w.eE};
-    EpiPhiAcc epi{w.acc, w.pairs, P2, (int)R, mom.np, K0 == 0 ? 1 : 0, 128};
-    constexpr int ST = (NPLA + NPLB) > 8 ? 2 : 3;
+    EpiPhiAcc epi{{}, w.acc, w.pairs, P2, (int)R, mom.np, K0 == 0 ? 1 : 0, 128};
+    // K = 4096 per chunk: a deep ring of 16-wide K steps keeps enough of the
+    // operand stream (the A pieces come from HBM) in flight
+    constexpr int ST = tc::max_stages<128, 16, NPLA, NPLB>();
     int st;
     if (R > 64) {
-      st = tc::launch_gemm<128, 32, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+      st = tc::launch_gemm<128, 16, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     } else if (R > 32) {
       epi.nt = 64;
       st = tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);

@@ -52,7 +52,7 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
   cfg.err = ctx->d_error;
   tc::Planes pa = planes_of(PA, K, M, batch, NPLA, ld);
   tc::Planes pb = planes_of(PB, K, N, batch, NPLB, ld);
-  EpiStoreC64 epi{C, (long long)M * N, N, N};
+  EpiStoreC64 epi{{}, C, (long long)M * N, N, N};
   constexpr int ST = (NPLA + NPLB) > 8 ? 2 : 3;
   if (N > 64) return tc::launch_gemm<128, 32, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
   if (N > 32) return tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);

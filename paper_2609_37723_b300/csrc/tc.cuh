@@ -139,11 +139,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // Instruction descriptor, kind::f16: D = F32, A/B = F16 or BF16, both
-// K-major, optional negation of A, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16, bool negA) {
+// K-major, optional negation of A or B, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16, bool negA, bool negB = false) {
   return (1u << 4)                                     // D format F32
          | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10)  // A, B format
          | ((negA ? 1u : 0u) << 13)                    // negate A
+         | ((negB ? 1u : 0u) << 14)                    // negate B
          | ((uint32_t)(N >> 3) << 17)                  // N / 8
          | ((uint32_t)(M >> 4) << 24);                 // M / 16
 }

@@ -49,6 +49,72 @@ struct GemmCfg {
   unsigned* err;
 };
 
+// Products of the split schemes, by operand planes: 3 x 4 pieces (6
+// products, fixed point) or 2 x 2 pieces (3 products).  A product (pa, pb,
+// acc) adds A[pa] B[pb] into accumulator pair acc.
+template <int NPLA, int NPLB>
+struct SchemeProducts;
+template <>
+struct SchemeProducts<6, 8> {
+  static constexpr int n = 6;
+  static constexpr int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 3, 2, 0}, acc[6] = {0, 1, 1, 1, 1, 1};
+};
+template <>
+struct SchemeProducts<4, 4> {
+  static constexpr int n = 3;
+  static constexpr int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0}, acc[3] = {0, 1, 1};
+};
+
+// One real MMA: A plane, B plane, accumulator (pair * 2 + re/im), negate B,
+// first write of its accumulator.
+struct MmaOp {
+  int ap, bp, dsel, negb, first;
+};
+
+// The 4 * nprod real MMAs of a 16-deep K step, grouped by A plane:
+//   A_re[pa]: D_re += A_re B_re[pb],   D_im += A_re B_im[pb]
+//   A_im[pa]: D_re += A_im (-B_im[pb]) (negate-B descriptor),  D_im += A_im B_re[pb]
+// Built at compile time, so the single issuing thread only adds constant
+// offsets to two descriptors per stage and keeps the tensor pipe fed (a
+// schedule decoded at run time left it waiting on the issuer).
+template <int NPLA, int NPLB>
+struct MmaSchedule {
+  using P = SchemeProducts<NPLA, NPLB>;
+  static constexpr int n = 4 * P::n;
+  MmaOp ops[4 * P::n];
+  constexpr MmaSchedule() : ops{} {
+    int k = 0;
+    bool written[4] = {false, false, false, false};
+    for (int pa = 0; pa < NPLA / 2; ++pa) {
+      for (int part = 0; part < 2; ++part) {
+        for (int p = 0; p < P::n; ++p) {
+          if (P::pa[p] != pa) continue;
+          const int br = 2 * P::pb[p], bi = br + 1, d = 2 * P::acc[p];
+          // D_re first, then D_im
+          const int b0 = part ? bi : br, b1 = part ? br : bi;
+          ops[k] = MmaOp{2 * pa + part, b0, d, part, written[d] ? 0 : 1};
+          written[d] = true;
+          ++k;
+          ops[k] = MmaOp{2 * pa + part, b1, d + 1, 0, written[d + 1] ? 0 : 1};
+          written[d + 1] = true;
+          ++k;
+        }
+      }
+    }
+  }
+};
+
+// Epilogue functors see each 16-column slice of a row, with a per-thread
+// State that lives across the slices of a tile: begin() before the first,
+// end() after the last (called by all 32 lanes of the warp together, also
+// for rows past M, so it may use warp shuffles).  Stateless epilogues
+// derive from this.
+struct EpiStateless {
+  struct State {};
+  __device__ __forceinline__ void begin(State&) const {}
+  __device__ __forceinline__ void end(State&, int) const {}
+};
+
 template <int NT, int KC, int NPLA, int NPLB>
 struct TileGeom {
   static constexpr int SWZ = KC * 2;  // bytes per tile row
@@ -62,6 +128,14 @@ struct TileGeom {
 template <int NT, int KC, int NPLA, int NPLB, int STAGES>
 constexpr size_t gemm_smem_bytes() {
   return (size_t)STAGES * TileGeom<NT, KC, NPLA, NPLB>::STAGE + 1024 /*align*/ + 256 /*barriers*/;
+}
+
+// Deepest ring (at most 6 stages) that fits the 227 KB of shared memory.
+template <int NT, int KC, int NPLA, int NPLB>
+constexpr int max_stages() {
+  constexpr size_t room = 232448 - 1024 - 256;
+  constexpr int s = (int)(room / TileGeom<NT, KC, NPLA, NPLB>::STAGE);
+  return s > 6 ? 6 : s;
 }
 
 constexpr int TC_THREADS = 64 + 8 * 32;  // producer, MMA issuer, 8 epilogue warps
@@ -134,9 +208,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     *(volatile uint32_t*)issued_s = issued;
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
-    const uint32_t id = idesc_f16(128, NT, BF16, false);
-    const uint32_t idn = idesc_f16(128, NT, BF16, true);
-    uint32_t started = 0;  // bit a: accumulator pair a has been written
+    constexpr uint32_t id = idesc_f16(128, NT, BF16, false);
+    constexpr uint32_t idn = idesc_f16(128, NT, BF16, false, true);
+    constexpr MmaSchedule<NPLA, NPLB> S{};
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (kb / STAGES) & 1;
@@ -145,25 +219,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * G::A_STAGE);
-      const uint32_t b0 = smem_u32(sB + s * G::B_STAGE);
+      // descriptors of the stage's first A / B rows; a plane or K offset
+      // adds (bytes >> 4) to the start-address field (no carry: < 256 KB)
+      const uint64_t da0 = smem_desc(smem_u32(sA + s * G::A_STAGE), G::SWZ);
+      const uint64_t db0 = smem_desc(smem_u32(sB + s * G::B_STAGE), G::SWZ);
+      const uint32_t acc0 = kb ? 1u : 0u;
 #pragma unroll
       for (int ks = 0; ks < KC / 16; ++ks) {
-        for (int p = 0; p < cfg.nprod; ++p) {
-          const uint32_t ar = a0 + (2 * cfg.pa[p]) * G::A_PLANE + ks * 32;
-          const uint32_t ai = ar + G::A_PLANE;
-          const uint32_t br = b0 + (2 * cfg.pb[p]) * G::B_PLANE + ks * 32;
-          const uint32_t bi = br + G::B_PLANE;
-          const uint64_t dar = smem_desc(ar, G::SWZ), dai = smem_desc(ai, G::SWZ);
-          const uint64_t dbr = smem_desc(br, G::SWZ), dbi = smem_desc(bi, G::SWZ);
-          const int a = cfg.acc[p];
-          const uint32_t d = tmem + (uint32_t)(a * 2 * NT);
-          const uint32_t accum = (started >> a) & 1u;
-          mma_f16(d, dar, dbr, id, accum);
-          mma_f16(d, dai, dbi, idn, 1u);
-          mma_f16(d + NT, dar, dbi, id, accum);
-          mma_f16(d + NT, dai, dbr, id, 1u);
-          started |= 1u << a;
+#pragma unroll
+        for (int o = 0; o < S.n; ++o) {
+          const MmaOp op = S.ops[o];
+          const uint64_t da = da0 + (uint64_t)((op.ap * G::A_PLANE + ks * 32) >> 4);
+          const uint64_t db = db0 + (uint64_t)((op.bp * G::B_PLANE + ks * 32) >> 4);
+          const uint32_t accum = (ks > 0 || !op.first) ? 1u : acc0;
+          const uint32_t d = tmem + (uint32_t)(op.dsel * NT);
+          mma_f16(d, da, db, op.negb ? idn : id, accum);
         }
       }
       mma_commit(&empty[s]);
@@ -177,6 +247,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     ok = __all_sync(0xffffffffu, ok && !*(volatile uint32_t*)abort_flag);  // warp-uniform for tcgen05.ld
     tc_fence_after();
     if (ok) {
+      typename Epi::State st;
+      epi.begin(st);
       const int row = m_tile * 128 + q * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
       const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
@@ -202,9 +274,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             re1[e] = __uint_as_float(r1[e]) * f1;
             im1[e] = __uint_as_float(i1[e]) * f1;
           }
-          epi(batch, row, col0, re0, re1, im0, im1);
+          epi(st, batch, row, col0, re0, re1, im0, im1);
         }
       }
+      epi.end(st, batch);
     }
     tc_fence_before();
   }

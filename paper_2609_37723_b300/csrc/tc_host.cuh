@@ -30,6 +30,16 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
     set_error("%s: K must be positive", name);
     return DISTIL_EINVAL;
   }
+  {  // the kernel's MMA schedule is compiled for the scheme of its plane counts
+    using P = SchemeProducts<NPLA, NPLB>;
+    bool same = cfg.nprod == P::n;
+    for (int p = 0; same && p < P::n; ++p)
+      same = cfg.pa[p] == P::pa[p] && cfg.pb[p] == P::pb[p] && cfg.acc[p] == P::acc[p];
+    if (!same) {
+      set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
+      return DISTIL_EINVAL;
+    }
+  }
   CUtensorMap ma, mb;
   DISTIL_TRY(encode_planes(&ma, A, 128, KC, BF16));
   DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));

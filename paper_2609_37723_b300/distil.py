@@ -34,7 +34,8 @@ EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_elementals_workspace", "distil_elementals",
            "distil_correlate_workspace", "distil_correlate", "distil_gevp",
            "distil_cgemm_workspace", "distil_cgemm", "distil_correlate_noalloc",
-           "distil_mode_supported", "distil_profile_enable", "distil_profile_read"]
+           "distil_mode_supported", "distil_profile_enable", "distil_profile_read",
+           "distil_device_status"]
 
 _lib = None
 _ctx = {}
@@ -53,6 +54,8 @@ class KernelStat(ctypes.Structure):
 def _declare(L):
     c_int, c_void_p, c_size_t = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
     P = ctypes.POINTER
+    L.distil_device_status.argtypes = [c_void_p, c_int, P(ctypes.c_uint)]
+    L.distil_device_status.restype = c_int
     L.distil_create.argtypes = [c_int, P(c_void_p)]
     L.distil_create.restype = c_int
     L.distil_destroy.argtypes = [c_void_p]
@@ -232,6 +235,14 @@ def gevp(C, t0: int, out=None, stream=None):
 
 def mode_available(mode) -> bool:
     return bool(lib().distil_mode_supported(_mode(mode)))
+
+
+def device_status(reset: bool = False, device: int = 0) -> int:
+    """Code of the first expired bounded device wait since the last reset
+    (0 = none); synchronises.  Raises DistilError when it is nonzero."""
+    code = ctypes.c_uint()
+    _check(lib().distil_device_status(context(device), int(reset), ctypes.byref(code)))
+    return int(code.value)
 
 
 def profile_enable(timing: bool = False, device: int = 0):
