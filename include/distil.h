@@ -29,6 +29,10 @@
  *  - Calls are asynchronous on the given CUDA stream (0 = legacy default
  *    stream) unless stated.  Workspace passed to a call must stay untouched
  *    until the stream has passed the call.
+ *  - Alignment: a workspace pointer must be 256-byte aligned (cudaMalloc
+ *    and torch allocations are); every array must be aligned to its element
+ *    (16 bytes for c128, 8 for c64 and f64).  Misaligned pointers are
+ *    rejected with DISTIL_EINVAL.
  *  - Every call returns a distil_status.  On error nothing has been
  *    enqueued (argument errors) or the stream may hold partial results
  *    (DISTIL_ECUDA, DISTIL_ETIMEOUT); distil_last_error() gives a message.

@@ -1,5 +1,6 @@
 // C-ABI entry points of libdistil (declared in include/distil.h): argument
 // validation, workspace accounting and dispatch to the kernels of each mode.
+#include <stdint.h>
 #include <stdarg.h>
 #include <string.h>
 
@@ -88,6 +89,8 @@ int distil_elementals_workspace(int L, int nt, int nv, int np, int mode, size_t*
   return DISTIL_OK;
 }
 
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
 int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv, const int32_t* mom, int np,
                       int mode, void* phi, void* workspace, size_t ws_bytes, distil_stream stream) {
   g_err[0] = 0;
@@ -97,6 +100,9 @@ int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv, con
   DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && np >= 1, "distil_elementals: nt, nv, np must be >= 1");
   DISTIL_CHECK_ARG(np <= EL_MAX_MOM, "distil_elementals: at most %d momenta per call", EL_MAX_MOM);
   DISTIL_CHECK_ARG(mom && ((v && phi) || comb3(nv) == 0), "distil_elementals: null pointer");
+  DISTIL_CHECK_ARG(aligned(v, mode == DISTIL_FP64 ? 16 : 8) && aligned(phi, mode == DISTIL_FP32 ? 8 : 16) &&
+                       aligned(workspace, 256),
+                   "distil_elementals: misaligned pointer (arrays to their element, workspace to 256 bytes)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (mode == DISTIL_FP64)
     return elementals_simt<double>(ctx, (const Cx<double>*)v, L, nt, nv, mom, np, (Cx<double>*)phi, s);
@@ -130,6 +136,10 @@ int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, 
   DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_correlate: nb=%d outside [1,16]", nb);
   DISTIL_CHECK_ARG(tau && prof && C && ((phi_snk && phi_src) || comb3(nv) == 0),
                    "distil_correlate: null pointer");
+  DISTIL_CHECK_ARG(aligned(phi_snk, mode == DISTIL_FP32 ? 8 : 16) && aligned(phi_src, mode == DISTIL_FP32 ? 8 : 16) &&
+                       aligned(tau, mode == DISTIL_FP64 ? 16 : 8) && aligned(prof, 8) && aligned(C, 16) &&
+                       aligned(workspace, 256),
+                   "distil_correlate: misaligned pointer (arrays to their element, workspace to 256 bytes)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   size_t need = 0;
   distil_correlate_workspace(nt, nv, np, nb, mode, &need);
@@ -171,6 +181,8 @@ int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, 
   DISTIL_CHECK_ARG(is_mixed(mode), "distil_cgemm: mode %d is not a tensor-core mode", mode);
   DISTIL_CHECK_ARG(M >= 1 && N >= 1 && K >= 1 && batch >= 1 && batch <= 65535, "distil_cgemm: bad sizes");
   DISTIL_CHECK_ARG(A && B && C && workspace, "distil_cgemm: null pointer");
+  DISTIL_CHECK_ARG(aligned(A, 8) && aligned(B, 8) && aligned(C, 8) && aligned(workspace, 256),
+                   "distil_cgemm: misaligned pointer (arrays to their element, workspace to 256 bytes)");
   size_t need = cgemm_workspace(mode, M, N, K, batch);
   if (ws_bytes < need) {
     set_error("distil_cgemm: workspace %zu < %zu bytes", ws_bytes, need);

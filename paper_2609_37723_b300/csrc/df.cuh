@@ -9,12 +9,15 @@
 
 namespace distil {
 
-struct DF {
+// Aligned like float2 / float4 so that arrays of them move with 8- and
+// 16-byte accesses (every array of them starts on a 256-byte boundary).
+struct __align__(8) DF {
   float hi, lo;
 };
-struct CDF {  // complex double-float, 16 bytes like complex128
+struct __align__(16) CDF {  // complex double-float, 16 bytes like complex128
   DF re, im;
 };
+static_assert(sizeof(DF) == 8 && sizeof(CDF) == 16, "double-float layout");
 
 __device__ __forceinline__ DF df_make(float hi, float lo) { DF r; r.hi = hi; r.lo = lo; return r; }
 

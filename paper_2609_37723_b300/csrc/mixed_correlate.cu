@@ -413,16 +413,19 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
   return ar.used + 256;
 }
 
-// GEMM with the N tile chosen from N (TMEM holds 4 x NT columns).
+// The mode contractions are short (K = N_v or 4 N_v): persistent GEMM with
+// two TMEM accumulator sets of 128 x 64 (or 128 x 32 for narrow N), so the
+// epilogue of one tile overlaps the MMAs of the next; 16-wide K steps in a
+// deep ring.
 template <bool BF16, int NPLA, int NPLB, class Epi>
 static int gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const tc::GemmCfg& cfg,
                 int batch, const Epi& epi, cudaStream_t s) {
-  constexpr int KC = 32;
-  constexpr int ST128 = (NPLA + NPLB) > 8 ? 2 : 3;
-  if (cfg.N > 64)
-    return tc::launch_gemm<128, KC, NPLA, NPLB, ST128, BF16>(ctx, name, A, B, cfg, batch, epi, s);
-  if (cfg.N > 32) return tc::launch_gemm<64, KC, NPLA, NPLB, 2, BF16>(ctx, name, A, B, cfg, batch, epi, s);
-  return tc::launch_gemm<32, KC, NPLA, NPLB, 2, BF16>(ctx, name, A, B, cfg, batch, epi, s);
+  constexpr int KC = 16;
+  if (cfg.N > 32)
+    return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(
+        ctx, name, A, B, cfg, batch, epi, s);
+  return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16>(
+      ctx, name, A, B, cfg, batch, epi, s);
 }
 
 static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }

@@ -129,6 +129,7 @@ template <int NT, int KC, int NPLA, int NPLB, int STAGES>
 constexpr size_t gemm_smem_bytes() {
   return (size_t)STAGES * TileGeom<NT, KC, NPLA, NPLB>::STAGE + 1024 /*align*/ + 256 /*barriers*/;
 }
+static_assert(2 * 8 * 6 + 5 * 8 + 16 <= 256, "barrier area: 2 x 6 ring barriers, 5 others, 3 words");
 
 // Deepest ring (at most 6 stages) that fits the 227 KB of shared memory.
 template <int NT, int KC, int NPLA, int NPLB>
@@ -289,6 +290,210 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
       if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
     }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+// Persistent variant for short contractions (K of a few hundred), where the
+// epilogue costs as much as the MMAs: one CTA per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... (same tile order as the one-tile
+// kernel's grid: n fastest, then m, then batch).  TMEM holds two
+// accumulator sets (2 x 4 NT columns), so the MMA warp fills one while the
+// epilogue warps drain the other; the TMA ring runs on across tiles.
+//   full[s] / empty[s]   TMA ring (producer <-> MMA)
+//   tfull[b]             MMA -> epilogue: accumulator set b is complete
+//   tempty[b]            epilogue -> MMA: set b has been read (8 warp arrivals)
+// Every wait is bounded; on expiry the error word is set, every role leaves
+// its loop, copies still in flight are waited for and TMEM is freed.
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                              GemmCfg cfg, Epi epi, int n_tiles, int m_tiles, int total_tiles) {
+  using G = TileGeom<NT, KC, NPLA, NPLB>;
+  static_assert(NT % 16 == 0 && NT >= 32 && 8 * NT <= 512, "two accumulator sets must fit TMEM");
+  static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
+  if (cfg.err && *(volatile unsigned*)cfg.err) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * G::A_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * G::B_STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint32_t* abort_flag = tslot + 1;
+  uint32_t* issued_s = tslot + 2;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (cfg.K + KC - 1) / KC;
+  constexpr uint32_t SET = 4 * NT;  // D0_re | D0_im | D1_re | D1_im
+  constexpr uint32_t TCOLS = 2 * SET;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    *issued_s = 0;
+    fence_mbar_init();
+    tma_prefetch(&mapA);
+    tma_prefetch(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, TCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  volatile uint32_t* abort_v = abort_flag;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    uint32_t g = 0;
+    for (int t = blockIdx.x; t < total_tiles && !*abort_v; t += gridDim.x) {
+      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      if (epi.skip_tile(m_tile, n_tile, batch)) continue;
+      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % STAGES);
+        const uint32_t ph = (g / STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT) || *abort_v) {
+          *abort_v = 1;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], G::STAGE);
+        tma_load_4d(&mapA, &full[s], sA + s * G::A_STAGE, kb * KC, m_tile * 128 + cfg.a.row_off, 0, ca);
+        tma_load_4d(&mapB, &full[s], sB + s * G::B_STAGE, kb * KC, n_tile * NT + cfg.b.row_off, 0, cb);
+        *(volatile uint32_t*)issued_s = g + 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    constexpr uint32_t id = idesc_f16(128, NT, BF16, false);
+    constexpr uint32_t idn = idesc_f16(128, NT, BF16, false, true);
+    constexpr MmaSchedule<NPLA, NPLB> S{};
+    uint32_t g = 0, it = 0;
+    for (int t = blockIdx.x; t < total_tiles && !*abort_v; t += gridDim.x) {
+      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      if (epi.skip_tile(m_tile, n_tile, batch)) continue;
+      const uint32_t buf = it & 1, use = it >> 1;
+      if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT) || *abort_v) {
+        *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dset = tmem + buf * SET;
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % STAGES);
+        const uint32_t ph = (g / STAGES) & 1;
+        if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *abort_v) {
+          *abort_v = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da0 = smem_desc(smem_u32(sA + s * G::A_STAGE), G::SWZ);
+        const uint64_t db0 = smem_desc(smem_u32(sB + s * G::B_STAGE), G::SWZ);
+        const uint32_t acc0 = kb ? 1u : 0u;
+#pragma unroll
+        for (int ks = 0; ks < KC / 16; ++ks) {
+#pragma unroll
+          for (int o = 0; o < S.n; ++o) {
+            const MmaOp op = S.ops[o];
+            const uint64_t da = da0 + (uint64_t)((op.ap * G::A_PLANE + ks * 32) >> 4);
+            const uint64_t db = db0 + (uint64_t)((op.bp * G::B_PLANE + ks * 32) >> 4);
+            const uint32_t accum = (ks > 0 || !op.first) ? 1u : acc0;
+            mma_f16(dset + (uint32_t)(op.dsel * NT), da, db, op.negb ? idn : id, accum);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      if (!ok) break;
+      mma_commit(&tfull[buf]);
+      ++it;
+    }
+    mma_commit(done);  // fires once every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;             // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;   // which half of the NT columns
+    uint32_t it = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      if (epi.skip_tile(m_tile, n_tile, batch)) continue;
+      const uint32_t buf = it & 1, use = it >> 1;
+      bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT);
+      ok = __all_sync(0xffffffffu, ok && !*abort_v);  // warp-uniform for tcgen05.ld
+      if (!ok) {
+        if (lane == 0) *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
+      typename Epi::State st;
+      epi.begin(st);
+      const int row = m_tile * 128 + q * 32 + lane;
+      const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
+      const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
+#pragma unroll 1
+      for (int c = half * (NT / 32); c < (half + 1) * (NT / 32); ++c) {
+        uint32_t r0[16], i0[16], r1[16], i1[16];
+        tmem_ld16(tl + c * 16, r0);
+        tmem_ld16(tl + NT + c * 16, i0);
+        tmem_ld16(tl + 2 * NT + c * 16, r1);
+        tmem_ld16(tl + 3 * NT + c * 16, i1);
+        tmem_wait_ld();
+        const int col0 = n_tile * NT + c * 16;
+        if (row < cfg.M) {
+          float re0[16], re1[16], im0[16], im1[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = col0 + e;
+            const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
+            const float f = pow2f(ea + eb - cfg.shift);  // exact power-of-two scalings
+            const float f1 = f * cfg.w1;
+            re0[e] = __uint_as_float(r0[e]) * f;
+            im0[e] = __uint_as_float(i0[e]) * f;
+            re1[e] = __uint_as_float(r1[e]) * f1;
+            im1[e] = __uint_as_float(i1[e]) * f1;
+          }
+          epi(st, batch, row, col0, re0, re1, im0, im1);
+        }
+      }
+      epi.end(st, batch);
+      // this warp is done reading set buf: hand it back to the MMA warp
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      ++it;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (*abort_v) {
+      // drain: wait (bounded) for the last load of every stage, so no copy
+      // lands in shared memory after the CTA has exited
+      const uint32_t issued = *(volatile uint32_t*)issued_s;
+      for (uint32_t g = issued > (uint32_t)STAGES ? issued - STAGES : 0; g < issued; ++g) {
+        if (!mbar_wait(&full[g % STAGES], (g / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
+      }
+    }
+    mbar_wait(done, 0, cfg.err, TC_ERR_DRAIN);  // every MMA has completed
   }
   __syncthreads();
   if (warp == 1) {

@@ -22,6 +22,16 @@ inline long long pad64(long long k) { return (k + 63) / 64 * 64; }
 
 int encode_planes(CUtensorMap* map, const Planes& t, int box_rows, int kc, bool bf16);
 
+// The kernel's MMA schedule is compiled for the scheme of its plane counts.
+template <int NPLA, int NPLB>
+bool products_match(const GemmCfg& cfg) {
+  using P = SchemeProducts<NPLA, NPLB>;
+  bool same = cfg.nprod == P::n;
+  for (int p = 0; same && p < P::n; ++p)
+    same = cfg.pa[p] == P::pa[p] && cfg.pb[p] == P::pb[p] && cfg.acc[p] == P::acc[p];
+  return same;
+}
+
 template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
 int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg,
                 int batch, const Epi& epi, cudaStream_t s) {
@@ -30,15 +40,9 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
     set_error("%s: K must be positive", name);
     return DISTIL_EINVAL;
   }
-  {  // the kernel's MMA schedule is compiled for the scheme of its plane counts
-    using P = SchemeProducts<NPLA, NPLB>;
-    bool same = cfg.nprod == P::n;
-    for (int p = 0; same && p < P::n; ++p)
-      same = cfg.pa[p] == P::pa[p] && cfg.pb[p] == P::pb[p] && cfg.acc[p] == P::acc[p];
-    if (!same) {
-      set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
-      return DISTIL_EINVAL;
-    }
+  if (!products_match<NPLA, NPLB>(cfg)) {
+    set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
+    return DISTIL_EINVAL;
   }
   CUtensorMap ma, mb;
   DISTIL_TRY(encode_planes(&ma, A, 128, KC, BF16));
@@ -59,6 +63,45 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
   {
     Launch L(ctx, name, s);
     kern<<<grid, TC_THREADS, smem, s>>>(ma, mb, cfg, epi);
+  }
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
+// Persistent launch: min(tiles, SMs) CTAs walk the 128 x NT tiles.
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
+int launch_gemm_persistent(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B,
+                           const GemmCfg& cfg, int batch, const Epi& epi, cudaStream_t s) {
+  if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
+  if (cfg.K <= 0) {
+    set_error("%s: K must be positive", name);
+    return DISTIL_EINVAL;
+  }
+  if (!products_match<NPLA, NPLB>(cfg)) {
+    set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
+    return DISTIL_EINVAL;
+  }
+  CUtensorMap ma, mb;
+  DISTIL_TRY(encode_planes(&ma, A, 128, KC, BF16));
+  DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
+  constexpr size_t smem = gemm_smem_bytes<NT, KC, NPLA, NPLB, STAGES>();
+  static_assert(smem <= 232448, "shared memory");
+  auto kern = tc_gemm_persistent_kernel<NT, KC, NPLA, NPLB, STAGES, BF16, Epi>;
+  static bool attr = false;
+  if (!attr) {
+    DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const long long n_tiles = (cfg.N + NT - 1) / NT, m_tiles = (cfg.M + 127) / 128;
+  const long long total = n_tiles * m_tiles * batch;
+  if (total > 0x7fffffffLL) {
+    set_error("%s: too many tiles", name);
+    return DISTIL_EINVAL;
+  }
+  const int grid = (int)(total < ctx->sm_count ? total : ctx->sm_count);
+  {
+    Launch L(ctx, name, s);
+    kern<<<grid, TC_THREADS, smem, s>>>(ma, mb, cfg, epi, (int)n_tiles, (int)m_tiles, (int)total);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;

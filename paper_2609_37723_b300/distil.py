@@ -154,6 +154,11 @@ def _workspace(nbytes: int, device):
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
+def _nbytes(workspace) -> int:
+    """Size of a caller's workspace tensor (the library checks it is enough)."""
+    return 0 if workspace is None else int(workspace.numel()) * int(workspace.element_size())
+
+
 def elementals(v, L: int, mom, mode="fp64", out=None, workspace=None, stream=None):
     """v: [nt][nv][L^3][3] complex tensor on the GPU; mom: [np][3] ints (host)."""
     import torch
@@ -174,7 +179,7 @@ def elementals(v, L: int, mom, mode="fp64", out=None, workspace=None, stream=Non
     _check(lib().distil_elementals(ctx, _ptr(v), L, nt, nv,
                                    mom_np.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), np_, mode,
                                    _ptr(out), _ptr(workspace) if workspace is not None else None,
-                                   ws_bytes, _stream(stream)))
+                                   _nbytes(workspace), _stream(stream)))
     return out
 
 
@@ -197,7 +202,7 @@ def correlate(phi_snk, phi_src, tau, prof, mode="fp64", prof_per_t: bool = False
     ctx = context(tau.device.index or 0)
     _check(lib().distil_correlate(ctx, _ptr(phi_snk), _ptr(phi_src), _ptr(tau), nt, nv, np_, _ptr(prof), nb,
                                   int(prof_per_t), mode, _ptr(out),
-                                  _ptr(workspace) if workspace is not None else None, ws_bytes,
+                                  _ptr(workspace) if workspace is not None else None, _nbytes(workspace),
                                   _stream(stream)))
     return out
 
@@ -218,7 +223,7 @@ def cgemm(A, B, mode="fp16x3", out=None, workspace=None, stream=None):
     if workspace is None:
         workspace = _workspace(b.value, A.device)
     _check(lib().distil_cgemm(context(A.device.index or 0), _ptr(A), _ptr(B), _ptr(out), M, N, K, batch, mode,
-                              _ptr(workspace), b.value, _stream(stream)))
+                              _ptr(workspace), _nbytes(workspace), _stream(stream)))
     return out
 
 

@@ -119,3 +119,23 @@ def test_chain_fp16x6_c1(cuda_lib):
     e = max_c_scaled_error(C.cpu().numpy(), ref_C)
     print(f"chain fp16x6 c1: scaled {e:.2e} strict {max_c_error(C.cpu().numpy(), ref_C):.2e}")
     assert e < 1e-6
+
+
+# ------------------------------------------------------------------ boundary checks
+
+def test_misaligned_workspace_rejected(cuda_lib):
+    """A workspace that is not 256-byte aligned is refused before any launch,
+    and the device status stays clean."""
+    import torch
+    from paper_2609_37723_b300 import distil
+    p = synth.config(1)
+    v = p.all_eigvecs().astype(np.complex64)
+    tau = p.all_perambulators().astype(np.complex64)
+    phi = orc.elementals(v, p.L, p.mom)
+    ws_bytes = distil.correlate_workspace(p.nt, p.nv, p.np_, p.nb, "fp16x6")
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(distil.DistilError, match="misaligned"):
+        distil.correlate(T(phi), T(phi[0]), T(tau), T(p.prof), "fp16x6", workspace=ws[16:])
+    got = distil.correlate(T(phi), T(phi[0]), T(tau), T(p.prof), "fp16x6", workspace=ws[256:]).cpu().numpy()
+    assert max_c_scaled_error(got, orc.correlator(phi, phi[0], tau, p.prof)) < TOL_C["fp16x6"]
+    assert distil.device_status() == 0
