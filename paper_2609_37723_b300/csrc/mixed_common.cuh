@@ -81,17 +81,29 @@ struct SliceBits {
   static constexpr int W = BF16 ? 8 : 11;
 };
 
+// Exact scaling by 2^n as two power-of-two factors, each in the normal
+// range for |n| <= 252 (the row exponents here stay far inside that).
+struct Pow2 {
+  float a, b;
+};
+__device__ __forceinline__ Pow2 pow2_pair(int n) {
+  const int h = n / 2;
+  return Pow2{tc::pow2f(h), tc::pow2f(n - h)};
+}
+__device__ __forceinline__ float scale2(float x, Pow2 s) { return (x * s.a) * s.b; }
+
 // NPC pieces of the double-float x for a row with exponent e and leading
-// slice width H (scheme notes above), in FP32 instructions: scaling by
-// powers of two is exact, t.hi - rint(t.hi) is exact, and adding t.lo to
-// that remainder rounds far below the last slice.
+// slice width H (scheme notes above), given s = 2^(H - e) (pow2_pair,
+// computed once per row), in FP32 instructions: scaling by powers of two is
+// exact, t.hi - rint(t.hi) is exact, and adding t.lo to that remainder
+// rounds far below the last slice.
 template <bool BF16, bool FIXED, int NPC>
-__device__ __forceinline__ void make_pieces(DF x, int e, int H, typename tc::Piece<BF16>::T (&p)[NPC]) {
+__device__ __forceinline__ void make_pieces(DF x, Pow2 s, typename tc::Piece<BF16>::T (&p)[NPC]) {
   using PC = tc::Piece<BF16>;
   constexpr int W = SliceBits<BF16>::W;
   if constexpr (FIXED) {
     constexpr float sw = (float)(1 << W), isw = 1.f / (float)(1 << W);
-    const float th = ldexpf(x.hi, H - e), tl = ldexpf(x.lo, H - e);
+    const float th = scale2(x.hi, s), tl = scale2(x.lo, s);
     const float hi = rintf(th);
     const float r1 = __fmul_rn(__fadd_rn(__fsub_rn(th, hi), tl), sw);
     const float mid = rintf(r1);
@@ -104,7 +116,7 @@ __device__ __forceinline__ void make_pieces(DF x, int e, int H, typename tc::Pie
       p[3] = PC::from(lo * isw);
     }
   } else {
-    float t = ldexpf(x.hi, H - e) + ldexpf(x.lo, H - e);
+    float t = scale2(x.hi, s) + scale2(x.lo, s);
 #pragma unroll
     for (int i = 0; i < NPC; ++i) {
       p[i] = PC::from(t);
@@ -144,14 +156,15 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
     exps[r] = e;
     if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
   }
+  const Pow2 sc = pow2_pair(H - e);
   const long long coord = r / rows_per, rr = r % rows_per;
   const long long ps = rows_per * ld;
   P16* base = out + coord * (2 * NPC) * ps + rr * ld;
   for (int k = lane; k < K; k += 32) {
     const CDF v = src(r, k);
     P16 pr[NPC], pi[NPC];
-    make_pieces<BF16, FIXED, NPC>(v.re, e, H, pr);
-    make_pieces<BF16, FIXED, NPC>(v.im, e, H, pi);
+    make_pieces<BF16, FIXED, NPC>(v.re, sc, pr);
+    make_pieces<BF16, FIXED, NPC>(v.im, sc, pi);
 #pragma unroll
     for (int i = 0; i < NPC; ++i) {
       base[(2 * i) * ps + k] = pr[i];
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, long lo
     if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
   }
   __syncthreads();
-  const int e = sh_e;
+  const Pow2 sc = pow2_pair(H - sh_e);
   const long long coord = r / rows_per, rr = r % rows_per;
   const long long ps = rows_per * ld;
   P16* base = out + coord * (2 * NPC) * ps + rr * ld;
@@ -204,8 +217,8 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, long lo
     const int k = threadIdx.x + 512 * u;
     if (k >= K) break;
     P16 pr[NPC], pi[NPC];
-    make_pieces<BF16, FIXED, NPC>(v[u].re, e, H, pr);
-    make_pieces<BF16, FIXED, NPC>(v[u].im, e, H, pi);
+    make_pieces<BF16, FIXED, NPC>(v[u].re, sc, pr);
+    make_pieces<BF16, FIXED, NPC>(v[u].im, sc, pi);
 #pragma unroll
     for (int i = 0; i < NPC; ++i) {
       base[(2 * i) * ps + k] = pr[i];

@@ -200,21 +200,31 @@ struct SSrc {  // rows b*P2 + pair(i'<j'), K = k': g g g conj(Phi_{i'j'k'})
   }
 };
 
-// eU[(a*3 + a')*n^2 + i'*n + k] = exponent of max_beta |Aa row (a'beta, i')| * max_j |G row (a, k, j)|
-__global__ void u_exponent_kernel(const float* __restrict__ nAa, const float* __restrict__ nG, int n, int nb,
+// mG[a*n + k] = max_j |G row (a, k, j)| (one warp per (a, k)).
+__global__ void g_rowmax_kernel(const float* __restrict__ nG, int n, int nb, float* __restrict__ mG) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)nb * n) return;
+  const float* g = nG + w * n;
+  float m = 0.f;
+  for (int j = lane; j < n; j += 32) m = fmaxf(m, g[j]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) mG[w] = m;
+}
+
+// eU[(a*3 + a')*n^2 + i'*n + k] = exponent of max_beta |Aa row (a'beta, i')| * max_j |G row (a, k, j)|,
+// a bound on every |U| of that row of the step-i output (Cauchy-Schwarz on the row norms).
+__global__ void u_exponent_kernel(const float* __restrict__ nAa, const float* __restrict__ mG, int n, int nb,
                                   int* __restrict__ eU) {
   const long long n2 = (long long)n * n;
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= 3LL * nb * n2) return;
   const int ab = (int)(e / n2);  // a*3 + a'
-  const int a = ab / 3, ap = ab % 3;
-  const int ip = (int)((e % n2) / n), k = (int)(e % n);
+  const int a = ab / 3, ap = ab - 3 * a;
+  const int r = (int)(e - ab * n2), ip = r / n, k = r - ip * n;
   float mA = 0.f;
   for (int beta = 0; beta < 4; ++beta) mA = fmaxf(mA, nAa[(ap * 4 + beta) * n + ip]);
-  float mG = 0.f;
-  const float* g = nG + (long long)a * n2 + (long long)k * n;
-  for (int j = 0; j < n; ++j) mG = fmaxf(mG, g[j]);
-  eU[e] = row_exponent(mA * mG * (1.f + 1e-5f));
+  eU[e] = row_exponent(mA * mG[a * n + k] * (1.f + 1e-5f));
 }
 
 // Step i epilogue: split U straight from the accumulator pair into the
@@ -238,15 +248,15 @@ struct EpiSplitU : tc::EpiStateless {
       // plane's 16 pieces in registers and write them as two 16-byte stores
       const int k = col0 / n, j0 = col0 % n;
       const long long ur = (long long)row * n + k;
-      const int ex = eU[(long long)aa * n2 + ur];
+      const Pow2 sc = pow2_pair(H - eU[(long long)aa * n2 + ur]);
       uint32_t w[2 * NPC][8];
 #pragma unroll
       for (int e = 0; e < 16; e += 2) {
         P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
-        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), ex, H, pr0);
-        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), ex, H, pi0);
-        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), ex, H, pr1);
-        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), ex, H, pi1);
+        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr0);
+        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi0);
+        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), sc, pr1);
+        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), sc, pi1);
 #pragma unroll
         for (int q = 0; q < NPC; ++q) {
           w[2 * q][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pr0[q]) |
@@ -270,10 +280,10 @@ struct EpiSplitU : tc::EpiStateless {
       if (c >= (int)n2) break;
       const int k = c / n, j = c % n;
       const long long ur = (long long)row * n + k;
-      const int ex = eU[(long long)aa * n2 + ur];
+      const Pow2 sc = pow2_pair(H - eU[(long long)aa * n2 + ur]);
       typename tc::Piece<BF16>::T pr[NPC], pi[NPC];
-      make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), ex, H, pr);
-      make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), ex, H, pi);
+      make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr);
+      make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi);
       auto* d = base + ur * ld4 + (long long)beta * n + j;
 #pragma unroll
       for (int q = 0; q < NPC; ++q) {
@@ -369,7 +379,7 @@ dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int 
 struct MixedWs {
   void *Aa, *TT, *Tc, *G, *S, *U;
   int *eAa, *eTT, *eTc, *eG, *eS, *eU;
-  float *nAa, *nG;
+  float *nAa, *nG, *mG;
   CDF *V, *X, *phs, *ph0;
   DF* g;
   int *etau, *esnk, *esrc;
@@ -396,6 +406,7 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, 
   w.eU = ar.take<int>(3 * nb * n2);
   w.nAa = ar.take<float>(12 * n);
   w.nG = ar.take<float>(nb * n2);
+  w.mG = ar.take<float>(nb * n);
   w.V = ar.take<CDF>((long long)nb * NPAIR * n3);
   w.X = ar.take<CDF>((long long)nb * NSRC * P2 * n);
   w.phs = ar.take<CDF>(T3);
@@ -452,7 +463,8 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
   DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_source", SSrc{w.ph0, g_src, nv, P2}, nb * P2, P2, nv, H, w.S, w.ldn, w.eS, s)));
   {
     Launch L(ctx, "u_exponent", s);
-    u_exponent_kernel<<<nblk(3 * nb * n2), 256, 0, s>>>(w.nAa, w.nG, nv, nb, w.eU);
+    g_rowmax_kernel<<<nblk(32LL * nb * n), 256, 0, s>>>(w.nG, nv, nb, w.mG);
+    u_exponent_kernel<<<nblk(3 * nb * n2), 256, 0, s>>>(w.nAa, w.mG, nv, nb, w.eU);
   }
   DISTIL_LAUNCH_CHECK();
 
@@ -495,7 +507,14 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
+    // K = 4 N_v: long enough for the one-tile kernel, whose 128-wide N tiles
+    // keep the MMAs fed better than the persistent kernel's 64-wide ones
+    if (cfg.N > 64) {
+      DISTIL_TRY((tc::launch_gemm<128, 16, NPLA, NPLB, tc::max_stages<128, 16, NPLA, NPLB>(), BF16>(
+          ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
+    } else {
+      DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
+    }
   }
   // ---- dot
   {

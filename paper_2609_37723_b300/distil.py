@@ -21,7 +21,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdistil.so")
+LIB_PATH = os.environ.get("DISTIL_LIBRARY") or os.path.join(HERE, "libdistil.so")  # another build of the library
 
 FP64, FP32, MIXED_BF16X6, MIXED_BF16X3, MIXED_FP16X3, MIXED_FP16X6 = 0, 1, 2, 3, 4, 5
 MODE_NAMES = {FP64: "fp64", FP32: "fp32", MIXED_BF16X6: "bf16x6", MIXED_BF16X3: "bf16x3",
