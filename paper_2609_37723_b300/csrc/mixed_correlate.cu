@@ -249,28 +249,28 @@ struct EpiSplitU : tc::EpiStateless {
       const int k = col0 / n, j0 = col0 % n;
       const long long ur = (long long)row * n + k;
       const Pow2 sc = pow2_pair(H - eU[(long long)aa * n2 + ur]);
-      uint32_t w[2 * NPC][8];
-#pragma unroll
-      for (int e = 0; e < 16; e += 2) {
-        P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
-        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr0);
-        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi0);
-        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), sc, pr1);
-        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), sc, pi1);
-#pragma unroll
-        for (int q = 0; q < NPC; ++q) {
-          w[2 * q][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pr0[q]) |
-                            ((uint32_t)reinterpret_cast<const uint16_t&>(pr1[q]) << 16);
-          w[2 * q + 1][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pi0[q]) |
-                                ((uint32_t)reinterpret_cast<const uint16_t&>(pi1[q]) << 16);
-        }
-      }
       P16* d = base + ur * ld4 + (long long)beta * n + j0;
 #pragma unroll
-      for (int pl = 0; pl < 2 * NPC; ++pl) {
-        uint4* d4 = reinterpret_cast<uint4*>(d + pl * ps);
-        d4[0] = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
-        d4[1] = make_uint4(w[pl][4], w[pl][5], w[pl][6], w[pl][7]);
+      for (int h = 0; h < 16; h += 8) {  // 8 columns at a time: one 16-byte store per plane
+        uint32_t w[2 * NPC][4];
+#pragma unroll
+        for (int e = h; e < h + 8; e += 2) {
+          P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
+          make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr0);
+          make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi0);
+          make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), sc, pr1);
+          make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), sc, pi1);
+#pragma unroll
+          for (int q = 0; q < NPC; ++q) {
+            w[2 * q][(e - h) / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pr0[q]) |
+                                    ((uint32_t)reinterpret_cast<const uint16_t&>(pr1[q]) << 16);
+            w[2 * q + 1][(e - h) / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pi0[q]) |
+                                        ((uint32_t)reinterpret_cast<const uint16_t&>(pi1[q]) << 16);
+          }
+        }
+#pragma unroll
+        for (int pl = 0; pl < 2 * NPC; ++pl)
+          *reinterpret_cast<uint4*>(d + pl * ps + h) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
       }
       return;
     }
@@ -424,10 +424,9 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
   return ar.used + 256;
 }
 
-// The mode contractions are short (K = N_v or 4 N_v): persistent GEMM with
-// two TMEM accumulator sets of 128 x 64 (or 128 x 32 for narrow N), so the
-// epilogue of one tile overlaps the MMAs of the next; 16-wide K steps in a
-// deep ring.
+// The short mode contractions (K = N_v): persistent GEMM with two TMEM
+// accumulator sets of 128 x 64 (128 x 32 for narrow N), so the epilogue of
+// one tile overlaps the MMAs of the next; 16-wide K steps in a deep ring.
 template <bool BF16, int NPLA, int NPLB, class Epi>
 static int gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const tc::GemmCfg& cfg,
                 int batch, const Epi& epi, cudaStream_t s) {
