@@ -166,44 +166,61 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- cpu baseline
 
+class OracleSlices:
+    """The FP64 oracle, as it stands, on (t, p = 0) slices of a workload: the
+    source elementals at t = 0 once (momentum 0), then per slice the sink
+    elementals of that t and momentum and that slice's C_ab(t).  Input
+    generation is not timed.  The source elementals serve every (t, p) slice
+    of the real workload, so a slice is charged 1/N_t of their time."""
+
+    def __init__(self, cid: int, nt: int = 0):
+        from oracle import nucleon as orc
+        self.orc = orc
+        p = synth.config(cid, 0)
+        if nt > 0:
+            p = dataclasses.replace(p, nt=min(p.nt, nt))
+        self.p = p
+        self.mom0 = p.mom[:1]
+        v0 = p.eigvecs(0)
+        t0 = time.perf_counter()
+        self.phi_src = orc.elementals_t(v0, p.L, self.mom0)[0]
+        self.src_s = time.perf_counter() - t0
+
+    def slice(self, t: int) -> float:
+        """Seconds of oracle work for slice t (source share included)."""
+        p = self.p
+        vt, tau = p.eigvecs(t), p.perambulator(t)
+        t0 = time.perf_counter()
+        phi = self.orc.elementals_t(vt, p.L, self.mom0)[0]
+        self.orc.correlator_tp(phi, self.phi_src, tau, p.prof, p.prof)
+        return time.perf_counter() - t0 + self.src_s / p.nt
+
+    @staticmethod
+    def cores() -> int:
+        try:
+            import threadpoolctl
+            info = threadpoolctl.threadpool_info()
+            return int(max(i.get("num_threads", 1) for i in info)) if info else 1
+        except Exception:
+            return os.cpu_count() or 1
+
+
 def cpu_baseline(cid: int, budget_s: float = 15.0) -> dict:
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    timeslices t = 1, 2, ... at momentum index 0 (elementals of that t and
-    momentum, then that C_ab(t)), plus the source elementals at t = 0,
-    until about `budget_s` seconds of CPU work are spent."""
-    from oracle import nucleon as orc
-    p = synth.config(cid, 0)
-    mom0 = p.mom[:1]
-    t0 = time.perf_counter()
-    v0 = p.eigvecs(0)
-    gen = time.perf_counter() - t0
-    t_start = time.perf_counter()
-    phi_src = orc.elementals_t(v0, p.L, mom0)[0]
-    done = 0
-    t = 1
-    gen_total = gen
-    while t < p.nt:
-        g0 = time.perf_counter()
-        vt = p.eigvecs(t)
-        tau = p.perambulator(t)
-        gen_total += time.perf_counter() - g0
-        phi = orc.elementals_t(vt, p.L, mom0)[0]
-        orc.correlator_tp(phi, phi_src, tau, p.prof, p.prof)
+    """The oracle on slices t = 1, 2, ... until about `budget_s` seconds of
+    CPU work are spent (at least one slice)."""
+    o = OracleSlices(cid)
+    p = o.p
+    elapsed, done = 0.0, 0
+    for t in range(1, max(2, p.nt)):
+        elapsed += o.slice(t if p.nt > 1 else 0)
         done += 1
-        t += 1
-        if time.perf_counter() - t_start - (gen_total - gen) > budget_s:
+        if elapsed > budget_s:
             break
-    elapsed = time.perf_counter() - t_start - (gen_total - gen)
     entries = done * p.nb * p.nb
-    try:
-        import threadpoolctl
-        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) if \
-            threadpoolctl.threadpool_info() else 1
-    except Exception:
-        cores = os.cpu_count()
-    return {"value": entries / elapsed, "unit": METRIC, "cores": int(cores), "kind": "oracle",
-            "sample": f"{done} (t, p=0) slices t=1..{done} of {p.nt * p.np_}, plus source elementals "
-                      f"at t=0; {elapsed:.1f} s; numpy FP64 with BLAS threads",
+    return {"value": entries / elapsed, "unit": METRIC, "cores": o.cores(), "kind": "oracle",
+            "sample": f"{done} (t, p=0) slice(s) of {p.nt * p.np_}: sink elementals + C_ab(t) each, plus "
+                      f"1/N_t of the t=0 source elementals ({o.src_s:.1f} s); {elapsed:.1f} s; "
+                      f"numpy FP64 with BLAS threads",
             "seconds": elapsed}
 
 
@@ -368,6 +385,123 @@ def run_ours(args):
     return out
 
 
+def run_ensemble(args):
+    """Workload 4: an ensemble of configurations with uneven N_v (N_v drawn
+    from {64, 96, 128} per configuration), sharded over ranks (configuration
+    c goes to rank c mod N), all of a rank's configurations in one
+    graph-captured plan (elementals -> correlator -> GEVP per
+    configuration) with autotuned tensor-core kernel variants."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    workers = min(32, os.cpu_count() or 1)
+    mine = [c for c in range(args.ncfg) if c % world == rank]
+    log(f"ensemble of {args.ncfg} configurations, rank {rank} takes {mine}")
+    host = [make_inputs(4, c, workers, args.nt) for c in mine]   # before any CUDA call
+    log("inputs ready: v %.2f GB" % (sum(h[1].nbytes for h in host) / 1e9))
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2609_37723_b300 import distil
+    mode = args.mode
+    if mode == "auto":
+        mode = next((m for m in ("fp16x6", "bf16x6") if distil.mode_available(m)), "fp32")
+    cdt = np.complex128 if mode == "fp64" else np.complex64
+    cfgs, pins = [], []
+    for p, v_h, tau_h in host:
+        v_pin = torch.from_numpy(np.ascontiguousarray(v_h.astype(cdt))).pin_memory()
+        tau_pin = torch.from_numpy(np.ascontiguousarray(tau_h.astype(cdt))).pin_memory()
+        prof_pin = torch.from_numpy(np.ascontiguousarray(p.prof)).pin_memory()
+        pins.append((v_pin, tau_pin, prof_pin))
+        cfgs.append({"nv": p.nv, "v": v_pin.to(dev), "tau": tau_pin.to(dev), "prof": prof_pin.to(dev),
+                     "C": torch.empty((p.np_, p.nb, p.nb, p.nt), dtype=torch.complex128, device=dev),
+                     "lam": torch.empty((p.np_, p.nt, p.nb), dtype=torch.complex128, device=dev)})
+    del host
+    p0 = synth.config(4, mine[0]) if mine else synth.config(4, 0)
+    if args.nt > 0:
+        p0 = dataclasses.replace(p0, nt=min(p0.nt, args.nt))
+    t0_gevp = min(2, p0.nt - 1)
+    plan = distil.Plan(p0.L, p0.nt, p0.mom, p0.nb, t0_gevp, mode, cfgs, autotune=True)
+    variants, kernels = plan.info()
+    log(f"plan: {len(cfgs)} configurations, {kernels} kernels per run, variants {variants}")
+    s = plan.stream
+    for i in range(args.warmup):
+        plan.run()
+        s.synchronize()
+        log(f"warm-up step {i} done")
+    entries = sum(p0.np_ * p0.nb * p0.nb * p0.nt for _ in cfgs)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(s)
+    for _ in range(args.steps):
+        plan.run()
+    ev1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    log(f"timed region: {ms / args.steps:.1f} ms per step")
+    tot = torch.tensor([float(entries), ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        ent = tot[:1].clone()
+        dist.all_reduce(ent, op=dist.ReduceOp.SUM)
+        mx = tot[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = torch.cat([ent, mx])
+    all_entries, ms_max = float(tot[0]), float(tot[1])
+    value = all_entries * args.steps / (ms_max / 1e3)
+
+    # end to end: host inputs in, C and lambda out, through the same plan
+    C_host = [torch.empty(c["C"].shape, dtype=c["C"].dtype).pin_memory() for c in cfgs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    e2e_steps = max(1, min(args.steps, 3))
+    with torch.cuda.stream(s):
+        for _ in range(e2e_steps):
+            for c, (vp, tp, pp) in zip(cfgs, pins):
+                c["v"].copy_(vp, non_blocking=True)
+                c["tau"].copy_(tp, non_blocking=True)
+                c["prof"].copy_(pp, non_blocking=True)
+            plan.run(s)
+            for c, ch in zip(cfgs, C_host):
+                ch.copy_(c["C"], non_blocking=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    h2d = sum(vp.nbytes + tp.nbytes + pp.nbytes for vp, tp, pp in pins)
+    d2h = sum(ch.numel() * 16 for ch in C_host)
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32"}.get(mode, mode + "(f32 accumulate)"),
+            "data": "synthetic (seeded orthonormal eigenvectors, Gaussian perambulators)",
+            "config": {"workload": f"L32_Nt64_ensemble{args.ncfg}", "L": p0.L, "nt": p0.nt,
+                       "nv": [c["nv"] for c in cfgs], "np": p0.np_, "nb": p0.nb, "mode": mode,
+                       "ncfg": args.ncfg, "parallelism": f"weak x{world} (configuration c on rank c mod N)",
+                       "graph": {"kernels_per_run": kernels, "variants": variants},
+                       "l2": "inputs larger than L2"},
+            "e2e": {"value": all_entries * e2e_steps / (ms_e2e / 1e3), "unit": "entries/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(kernels * args.steps),
+            "clocks": clk, "parity": None, "cpu_baseline": None,
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
 def kernel_cmacs(name, p):
     """Complex MACs one step asks of a kernel family (the per-unit counts of
     the contraction each family runs, times the units per step)."""
@@ -435,19 +569,30 @@ def parity_slice(p, v_h, tau_h, C_gpu, mode):
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, one
+    (t, p = 0) slice of the same workload per step (untimed warm-up slices
+    first), entries/s = N_B^2 per slice / mean timed slice time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    p = synth.config(args.workload, 0)
-    cb = cpu_baseline(args.workload, args.cpu_budget)
-    steps_ms = []
-    for _ in range(args.warmup + args.steps):
-        pass
-    val = cb["value"]
+    cid = 3 if args.workload == 4 else args.workload
+    o = OracleSlices(cid, args.nt)
+    p = o.p
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = 1 + i % (p.nt - 1) if p.nt > 1 else 0
+        dt = o.slice(t)
+        log(f"reference slice t={t}: {dt:.1f} s")
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    val = p.nb * p.nb / (ms / 1e3)
+    cb = {"value": val, "unit": METRIC, "cores": o.cores(), "kind": "oracle",
+          "sample": f"{args.steps} timed (t, p=0) slices after {args.warmup} untimed: sink elementals + "
+                    f"C_ab(t) each, plus 1/N_t of the t=0 source elementals ({o.src_s:.1f} s)"}
     return {"metric": METRIC, "value": val, "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": p.np_ * p.nb * p.nb * p.nt / val * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": p.name, "L": p.L, "nt": p.nt, "nv": p.nv, "np": p.np_, "nb": p.nb},
             "cpu_baseline": cb,
             "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -464,10 +609,17 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--ncfg", type=int, default=4,
+                    help="workload 4: configurations in the ensemble (16 in full; each holds 3-6 GB of inputs)")
     ap.add_argument("--nt", type=int, default=0,
                     help="keep only the first NT timeslices (profiling a smaller case; not a bench number)")
     args = ap.parse_args()
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        out = run_reference(args)
+    elif args.workload == 4:
+        out = run_ensemble(args)
+    else:
+        out = run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

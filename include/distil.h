@@ -203,6 +203,69 @@ int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* p
                              void* C, distil_stream stream);
 
 /* ------------------------------------------------------------------ */
+/* Batched ensembles: tuning, graph-captured plans                     */
+/* ------------------------------------------------------------------ */
+
+/* Tensor-core kernel variant of each mode-contraction site of the mixed
+ * correlator, variants[3] = {step i, step j, source}: 0 = one 128 x 128
+ * tile per CTA, 1 = persistent CTAs with two 128 x 64 accumulator sets.
+ * Every variant gives identical results; only the speed differs.  The
+ * defaults are {1, 0, 1}.  The library has no counterpart of this in the
+ * paper: it is a property of this implementation. */
+int distil_set_tuning(distil_ctx* ctx, const int* variants);
+int distil_get_tuning(const distil_ctx* ctx, int* variants);
+
+/* An ensemble of gauge configurations sharing L, nt, the momenta, nb and
+ * the mode, each with its own N_v (Sec. 2.1: the correlators of a
+ * configuration follow from its eigenvectors and perambulators; the
+ * paper's ensembles are processed configuration by configuration). */
+typedef struct {
+  int L, nt, np, nb;
+  int t0;                /* GEVP reference timeslice, 0 <= t0 < nt */
+  int mode;              /* distil_mode */
+  const int32_t* mom;    /* [np][3] integers (host), p = 2 pi n / L */
+} distil_batch_shape;
+
+typedef struct {
+  int nv;                /* eigenvectors of this configuration (>= 1) */
+  const void* v;         /* [nt][nv][L^3][3] c128 (FP64 mode) or c64, device */
+  const void* tau;       /* [nt][4nv][4nv] c128 (FP64) or c64, device, tau(t, 0) */
+  const double* prof;    /* [nb][nv] f64, device */
+  void* C;               /* [np][nb][nb][nt] c128 output, device */
+  void* lambda;          /* [np][nt][nb] c128 GEVP output, device, or NULL */
+} distil_batch_cfg;
+
+typedef struct distil_plan distil_plan;
+
+/* Bytes of workspace a plan over these configurations needs: the largest
+ * configuration's elementals plus the largest elementals / correlator
+ * workspace.  No device needed. */
+int distil_plan_workspace(const distil_batch_shape* shape, const distil_batch_cfg* cfgs, int ncfg,
+                          size_t* bytes);
+
+/* Build a plan: optionally autotune (autotune != 0: run the correlator of
+ * the first configuration on its first timeslice once per kernel variant,
+ * with event timing, and keep the faster variant of every site; this runs
+ * eagerly on `stream`, synchronises it and resets the context's kernel
+ * statistics), then capture, on `stream`, the whole ensemble (per
+ * configuration: elementals, correlator with the source at t = 0, GEVP)
+ * into one CUDA graph.  The workspace is used by every run of the plan and
+ * must outlive it; the cfgs pointers are captured into the graph.  The
+ * plan sets ctx's tuning table to the variants it chose. */
+int distil_plan_create(distil_ctx* ctx, const distil_batch_shape* shape, const distil_batch_cfg* cfgs, int ncfg,
+                       int autotune, void* workspace, size_t ws_bytes, distil_stream stream, distil_plan** out);
+
+/* Launch the captured graph on `stream` (asynchronous).  Plans of one
+ * context share the context's device error word. */
+int distil_plan_run(distil_plan* plan, distil_stream stream);
+
+/* The variants the plan was captured with, variants[3] as in
+ * distil_set_tuning, and the number of kernel launches in its graph. */
+int distil_plan_info(const distil_plan* plan, int* variants, int* kernels);
+
+void distil_plan_destroy(distil_plan* plan);
+
+/* ------------------------------------------------------------------ */
 /* Introspection                                                       */
 /* ------------------------------------------------------------------ */
 

@@ -59,6 +59,9 @@ int distil_create(int device, distil_ctx** out) {
   c->cc_minor = prop.minor;
   c->d_error = nullptr;
   c->prof = new Profiler();
+  c->tune[0] = 1;  // step i (K = N_v): persistent, epilogue overlapped
+  c->tune[1] = 0;  // step j (K = 4 N_v): one 128 x 128 tile per CTA
+  c->tune[2] = 1;  // source (K = N_v): persistent
   if (cudaMalloc(&c->d_error, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMemset(c->d_error, 0, sizeof(unsigned int) * 4) != cudaSuccess) {
     set_error("distil_create: cannot allocate the device error word");
@@ -194,6 +197,22 @@ int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, 
 int distil_mode_supported(int mode) {
   if (!valid_mode(mode)) return 0;
   return is_mixed(mode) ? mixed_mode_built(mode) : 1;
+}
+
+int distil_set_tuning(distil_ctx* ctx, const int* variants) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(ctx != nullptr && variants != nullptr, "distil_set_tuning: null pointer");
+  for (int i = 0; i < 3; ++i)
+    DISTIL_CHECK_ARG(variants[i] == 0 || variants[i] == 1, "distil_set_tuning: variant %d of site %d", variants[i], i);
+  for (int i = 0; i < 3; ++i) ctx->tune[i] = variants[i];
+  return DISTIL_OK;
+}
+
+int distil_get_tuning(const distil_ctx* ctx, int* variants) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(ctx != nullptr && variants != nullptr, "distil_get_tuning: null pointer");
+  for (int i = 0; i < 3; ++i) variants[i] = ctx->tune[i];
+  return DISTIL_OK;
 }
 
 int distil_device_status(distil_ctx* ctx, int reset, unsigned* code) {

@@ -125,4 +125,9 @@ struct distil_ctx {
   int cc_major, cc_minor;
   unsigned int* d_error;   // device error word for bounded waits (0 = ok)
   distil::Profiler* prof;  // launch counts and optional event timing
+  // tensor-core kernel variant of each mode-contraction site (step i,
+  // step j, source): 0 = one 128 x 128 tile per CTA, 1 = persistent CTAs
+  // with two 128 x 64 accumulator sets; set by distil_set_tuning or the
+  // plan autotuner
+  int tune[3];
 };

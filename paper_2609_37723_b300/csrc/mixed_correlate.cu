@@ -313,11 +313,13 @@ __device__ __forceinline__ CDF ldg_cdf(const CDF* p) {  // p is 16-byte aligned
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
   return cdf_make(df_make(v.x, v.y), df_make(v.z, v.w));
 }
+// Each block leaves its partial sums in part[block][a][b] (FP64); a second
+// kernel adds the blocks in a fixed order, so C is the same to the last bit
+// from run to run (and graph replay to replay).
+constexpr int DOT_BLOCKS = 1184;  // 8 x 148 SMs
 template <int MAXB>
 __global__ void __launch_bounds__(32 * MAXB)
-dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int nb, const int* __restrict__ etau,
-              const int* __restrict__ esnk, const int* __restrict__ esrc, Cx<double>* __restrict__ C,
-              long long cstride_a, long long cstride_b) {
+dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int nb, Cx<double>* __restrict__ part) {
   const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (a >= nb) return;
   const long long P2 = comb2(nv);
@@ -358,7 +360,6 @@ dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int 
       }
     }
   }
-  const double scale = ldexp(1.0, 3 * etau[0] + esnk[0] + esrc[0]);
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) {
     if (b >= nb) break;
@@ -368,10 +369,43 @@ dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int 
       vi = df_add(vi, df_make(__shfl_xor_sync(0xffffffffu, vi.hi, o), __shfl_xor_sync(0xffffffffu, vi.lo, o)));
     }
     if (lane == 0) {
-      double* dst = reinterpret_cast<double*>(C + a * cstride_a + b * cstride_b);
-      atomicAdd(dst, df_to_double(vr) * scale);
-      atomicAdd(dst + 1, df_to_double(vi) * scale);
+      Cx<double>& dst = part[((long long)blockIdx.x * nb + a) * nb + b];
+      dst.r = df_to_double(vr);
+      dst.i = df_to_double(vi);
     }
+  }
+}
+
+// C[a][b] = 2^scale sum over blocks of part[block][a][b]: one block of 256
+// threads per (a, b), each thread summing a fixed stride of the blocks, then
+// a fixed-shape tree, so the order of the additions never changes.
+__global__ void __launch_bounds__(256)
+dot_reduce_kernel(const Cx<double>* __restrict__ part, int nblocks, int nb, const int* __restrict__ etau,
+                  const int* __restrict__ esnk, const int* __restrict__ esrc, Cx<double>* __restrict__ C,
+                  long long cstride_a, long long cstride_b) {
+  __shared__ double sr[256], si[256];
+  const int ab = blockIdx.x;
+  double zr = 0.0, zi = 0.0;
+  for (int k = threadIdx.x; k < nblocks; k += 256) {
+    const Cx<double> p = part[(long long)k * nb * nb + ab];
+    zr += p.r;
+    zi += p.i;
+  }
+  sr[threadIdx.x] = zr;
+  si[threadIdx.x] = zi;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sr[threadIdx.x] += sr[threadIdx.x + h];
+      si[threadIdx.x] += si[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double scale = ldexp(1.0, 3 * etau[0] + esnk[0] + esrc[0]);
+    Cx<double>& dst = C[(ab / nb) * cstride_a + (ab % nb) * cstride_b];
+    dst.r = sr[0] * scale;
+    dst.i = si[0] * scale;
   }
 }
 
@@ -381,6 +415,7 @@ struct MixedWs {
   int *eAa, *eTT, *eTc, *eG, *eS, *eU;
   float *nAa, *nG, *mG;
   CDF *V, *X, *phs, *ph0;
+  Cx<double>* part;
   DF* g;
   int *etau, *esnk, *esrc;
   long long ldn, ld4;
@@ -408,6 +443,7 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, 
   w.nG = ar.take<float>(nb * n2);
   w.mG = ar.take<float>(nb * n);
   w.V = ar.take<CDF>((long long)nb * NPAIR * n3);
+  w.part = ar.take<Cx<double>>((long long)DOT_BLOCKS * nb * nb);
   w.X = ar.take<CDF>((long long)nb * NSRC * P2 * n);
   w.phs = ar.take<CDF>(T3);
   w.ph0 = ar.take<CDF>(T3);
@@ -424,18 +460,32 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
   return ar.used + 256;
 }
 
-// The short mode contractions (K = N_v): persistent GEMM with two TMEM
-// accumulator sets of 128 x 64 (128 x 32 for narrow N), so the epilogue of
-// one tile overlaps the MMAs of the next; 16-wide K steps in a deep ring.
+// Mode-contraction GEMM in the kernel variant the context's tuning table
+// names for this site: 0 = one 128 x 128 tile per CTA (wide MMAs, no
+// overlap of epilogue and MMAs), 1 = persistent CTAs with two 128 x 64
+// accumulator sets (the epilogue of one tile overlaps the MMAs of the
+// next).  Both accumulate every element over K in the same order, so they
+// give identical results.
+enum GemmSite { SITE_STEP_I = 0, SITE_STEP_J = 1, SITE_SOURCE = 2 };
 template <bool BF16, int NPLA, int NPLB, class Epi>
-static int gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const tc::GemmCfg& cfg,
-                int batch, const Epi& epi, cudaStream_t s) {
+static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& A, const Planes& B,
+                const tc::GemmCfg& cfg, int batch, const Epi& epi, cudaStream_t s) {
   constexpr int KC = 16;
-  if (cfg.N > 32)
-    return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(
+  if (ctx->tune[site] == 1) {
+    if (cfg.N > 32)
+      return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(
+          ctx, name, A, B, cfg, batch, epi, s);
+    return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16>(
         ctx, name, A, B, cfg, batch, epi, s);
-  return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16>(
-      ctx, name, A, B, cfg, batch, epi, s);
+  }
+  if (cfg.N > 64)
+    return tc::launch_gemm<128, KC, NPLA, NPLB, tc::max_stages<128, KC, NPLA, NPLB>(), BF16>(ctx, name, A, B, cfg,
+                                                                                            batch, epi, s);
+  if (cfg.N > 32)
+    return tc::launch_gemm<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(ctx, name, A, B, cfg,
+                                                                                          batch, epi, s);
+  return tc::launch_gemm<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16>(ctx, name, A, B, cfg,
+                                                                                        batch, epi, s);
 }
 
 static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
@@ -479,7 +529,7 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
     cfg.b = tc::OpMap{12, nb, 1, 0, 0, (int)n2, w.eG};
     EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
   }
   // ---- source: batch (b, c) = nb x 5; X[b][c][pair][k]
   {
@@ -492,7 +542,7 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.out = w.X;
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
     epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, SITE_SOURCE, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
   }
   // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
@@ -506,25 +556,19 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
-    // K = 4 N_v: long enough for the one-tile kernel, whose 128-wide N tiles
-    // keep the MMAs fed better than the persistent kernel's 64-wide ones
-    if (cfg.N > 64) {
-      DISTIL_TRY((tc::launch_gemm<128, 16, NPLA, NPLB, tc::max_stages<128, 16, NPLA, NPLB>(), BF16>(
-          ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
-    } else {
-      DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
-    }
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
   }
   // ---- dot
   {
     const long long work = P2 * n;
     unsigned gx = (unsigned)((work + 31) / 32);
-    if (gx > 1184) gx = 1184;
+    if (gx > (unsigned)DOT_BLOCKS) gx = DOT_BLOCKS;
     Launch L(ctx, "dot", s);
     if (nb <= 8)
-      dot_df_kernel<8><<<gx, 32 * 8, 0, s>>>(w.V, w.X, nv, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
+      dot_df_kernel<8><<<gx, 32 * 8, 0, s>>>(w.V, w.X, nv, nb, w.part);
     else
-      dot_df_kernel<16><<<gx, 32 * 16, 0, s>>>(w.V, w.X, nv, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
+      dot_df_kernel<16><<<gx, 32 * 16, 0, s>>>(w.V, w.X, nv, nb, w.part);
+    dot_reduce_kernel<<<nb * nb, 256, 0, s>>>(w.part, (int)gx, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;

@@ -35,7 +35,9 @@ EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_correlate_workspace", "distil_correlate", "distil_gevp",
            "distil_cgemm_workspace", "distil_cgemm", "distil_correlate_noalloc",
            "distil_mode_supported", "distil_profile_enable", "distil_profile_read",
-           "distil_device_status"]
+           "distil_device_status", "distil_set_tuning", "distil_get_tuning",
+           "distil_plan_workspace", "distil_plan_create", "distil_plan_run", "distil_plan_info",
+           "distil_plan_destroy"]
 
 _lib = None
 _ctx = {}
@@ -51,11 +53,38 @@ class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
 
 
+class BatchShape(ctypes.Structure):
+    """distil_batch_shape: what every configuration of an ensemble shares."""
+    _fields_ = [("L", ctypes.c_int), ("nt", ctypes.c_int), ("np", ctypes.c_int), ("nb", ctypes.c_int),
+                ("t0", ctypes.c_int), ("mode", ctypes.c_int), ("mom", ctypes.POINTER(ctypes.c_int32))]
+
+
+class BatchCfg(ctypes.Structure):
+    """distil_batch_cfg: one configuration (device pointers)."""
+    _fields_ = [("nv", ctypes.c_int), ("v", ctypes.c_void_p), ("tau", ctypes.c_void_p),
+                ("prof", ctypes.c_void_p), ("C", ctypes.c_void_p), ("lam", ctypes.c_void_p)]
+
+
 def _declare(L):
     c_int, c_void_p, c_size_t = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
     P = ctypes.POINTER
     L.distil_device_status.argtypes = [c_void_p, c_int, P(ctypes.c_uint)]
     L.distil_device_status.restype = c_int
+    L.distil_set_tuning.argtypes = [c_void_p, P(c_int)]
+    L.distil_set_tuning.restype = c_int
+    L.distil_get_tuning.argtypes = [c_void_p, P(c_int)]
+    L.distil_get_tuning.restype = c_int
+    L.distil_plan_workspace.argtypes = [P(BatchShape), P(BatchCfg), c_int, P(c_size_t)]
+    L.distil_plan_workspace.restype = c_int
+    L.distil_plan_create.argtypes = [c_void_p, P(BatchShape), P(BatchCfg), c_int, c_int, c_void_p, c_size_t,
+                                     c_void_p, P(c_void_p)]
+    L.distil_plan_create.restype = c_int
+    L.distil_plan_run.argtypes = [c_void_p, c_void_p]
+    L.distil_plan_run.restype = c_int
+    L.distil_plan_info.argtypes = [c_void_p, P(c_int), P(c_int)]
+    L.distil_plan_info.restype = c_int
+    L.distil_plan_destroy.argtypes = [c_void_p]
+    L.distil_plan_destroy.restype = None
     L.distil_create.argtypes = [c_int, P(c_void_p)]
     L.distil_create.restype = c_int
     L.distil_destroy.argtypes = [c_void_p]
@@ -262,3 +291,81 @@ def profile_read(device: int = 0) -> dict:
     arr = (KernelStat * max(1, n.value))()
     _check(lib().distil_profile_read(context(device), arr, n.value, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(n.value)}
+
+
+# ------------------------------------------------------------------ tuning and batched plans
+
+def set_tuning(variants, device: int = 0):
+    """Kernel variant of each mode-contraction site {step i, step j, source}:
+    0 = one 128 x 128 tile per CTA, 1 = persistent, overlapped epilogue."""
+    arr = (ctypes.c_int * 3)(*[int(x) for x in variants])
+    _check(lib().distil_set_tuning(context(device), arr))
+
+
+def get_tuning(device: int = 0):
+    arr = (ctypes.c_int * 3)()
+    _check(lib().distil_get_tuning(context(device), arr))
+    return list(arr)
+
+
+def _batch(L, nt, mom, nb, t0, mode, cfgs):
+    mom_np = np.ascontiguousarray(np.asarray(mom, dtype=np.int32).reshape(-1, 3))
+    shape = BatchShape(int(L), int(nt), int(mom_np.shape[0]), int(nb), int(t0), _mode(mode),
+                       mom_np.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    arr = (BatchCfg * len(cfgs))()
+    for i, c in enumerate(cfgs):
+        arr[i] = BatchCfg(int(c["nv"]), c["v"].data_ptr() if "v" in c else None,
+                          c["tau"].data_ptr() if "tau" in c else None,
+                          c["prof"].data_ptr() if "prof" in c else None,
+                          c["C"].data_ptr() if "C" in c else None,
+                          c["lam"].data_ptr() if c.get("lam") is not None else None)
+    return shape, arr, mom_np
+
+
+def plan_workspace(L, nt, mom, nb, mode, nvs) -> int:
+    """Workspace bytes of a plan over configurations with these N_v (no device needed)."""
+    shape, arr, _keep = _batch(L, nt, mom, nb, 0, mode, [{"nv": nv} for nv in nvs])
+    b = ctypes.c_size_t()
+    _check(lib().distil_plan_workspace(ctypes.byref(shape), arr, len(nvs), ctypes.byref(b)))
+    return b.value
+
+
+class Plan:
+    """An ensemble of configurations (shared L, nt, momenta, nb, mode; each
+    with its own N_v) captured into one CUDA graph.  cfgs: list of dicts
+    with device tensors v, tau, prof (f64 [nb][nv]) and outputs C
+    ([np][nb][nb][nt] c128) and optionally lam ([np][nt][nb] c128)."""
+
+    def __init__(self, L, nt, mom, nb, t0, mode, cfgs, autotune=True, stream=None):
+        import torch
+        self.cfgs = cfgs
+        dev = cfgs[0]["v"].device
+        self.device = dev.index or 0
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        shape, arr, self._mom = _batch(L, nt, mom, nb, t0, mode, cfgs)
+        b = ctypes.c_size_t()
+        _check(lib().distil_plan_workspace(ctypes.byref(shape), arr, len(cfgs), ctypes.byref(b)))
+        self.workspace = torch.empty(b.value, dtype=torch.uint8, device=dev)
+        torch.cuda.current_stream(dev).synchronize()   # inputs written on other streams are visible
+        h = ctypes.c_void_p()
+        _check(lib().distil_plan_create(context(self.device), ctypes.byref(shape), arr, len(cfgs), int(autotune),
+                                        _ptr(self.workspace), b.value, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        s = self.stream if stream is None else stream
+        _check(lib().distil_plan_run(self.handle, ctypes.c_void_p(s.cuda_stream)))
+
+    def info(self):
+        v = (ctypes.c_int * 3)()
+        k = ctypes.c_int()
+        _check(lib().distil_plan_info(self.handle, v, ctypes.byref(k)))
+        return list(v), int(k.value)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.distil_plan_destroy(h)
+            self.handle = None
+

@@ -68,3 +68,34 @@ def test_create_without_gpu_fails_cleanly(L):
     assert st in (1, 3)
     assert h.value is None
     assert len(L.distil_last_error()) > 0
+
+
+def test_plan_workspace_host_logic(L):
+    """A plan's workspace is the largest configuration's elementals plus the
+    largest elementals / correlator workspace: it grows with the largest N_v
+    and does not depend on how many smaller configurations come with it."""
+    mom = [(0, 0, 0), (1, 0, 0)]
+    one = distil.plan_workspace(4, 3, mom, 2, "fp16x6", [16])
+    many = distil.plan_workspace(4, 3, mom, 2, "fp16x6", [6, 16, 11, 16])
+    small = distil.plan_workspace(4, 3, mom, 2, "fp16x6", [6, 11])
+    assert one == many > small > 0
+    phi16 = 3 * 2 * distil.n_triples(16) * 16
+    assert one >= phi16
+    # FP64 plan: elementals in c128, no tensor-core workspace
+    assert distil.plan_workspace(4, 3, mom, 2, "fp64", [16]) >= phi16
+
+
+def test_plan_rejects_bad_ensembles(L):
+    mom = [(0, 0, 0)]
+    with pytest.raises(distil.DistilError, match="nv < 1"):
+        distil.plan_workspace(4, 3, mom, 2, "fp16x6", [8, 0])
+    shape, arr, _keep = distil._batch(4, 3, mom, 2, 5, "fp16x6", [{"nv": 8}])   # t0 = 5 >= nt
+    b = ctypes.c_size_t()
+    assert L.distil_plan_workspace(ctypes.byref(shape), arr, 1, ctypes.byref(b)) == 1
+    assert b"t0" in L.distil_last_error()
+    assert L.distil_plan_workspace(ctypes.byref(shape), arr, 0, ctypes.byref(b)) == 1
+    # a null context or plan is refused without touching a device
+    h = ctypes.c_void_p()
+    assert L.distil_plan_create(None, ctypes.byref(shape), arr, 1, 0, None, 0, None, ctypes.byref(h)) == 1
+    assert L.distil_plan_run(None, None) == 1
+    L.distil_plan_destroy(None)
