@@ -224,6 +224,28 @@ def cpu_baseline(cid: int, budget_s: float = 15.0) -> dict:
             "seconds": elapsed}
 
 
+# --------------------------------------------------------------------------- ranks
+
+def shard_configs(ncfg: int, rank: int, world: int) -> list:
+    """Configurations of an ensemble handled by `rank`: c with c mod world = rank
+    (independent problems: no data-path collective)."""
+    return [c for c in range(ncfg) if c % world == rank]
+
+
+def job_throughput(entries_local: float, ms_local: float, steps: int, dist=None, device=None):
+    """Whole-job throughput: entries summed over ranks / the slowest rank's
+    time.  Returns (entries/s, all entries per step, max ms)."""
+    import torch
+    t = torch.tensor([float(entries_local), float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        e, m = t[:1].clone(), t[1:].clone()
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        t = torch.cat([e, m])
+    all_entries, ms_max = float(t[0]), float(t[1])
+    return all_entries * steps / (ms_max / 1e3), all_entries, ms_max
+
+
 # --------------------------------------------------------------------------- ours
 
 def peaks():
@@ -313,13 +335,9 @@ def run_ours(args):
     log(f"timed region: {ms / args.steps:.1f} ms per step")
     kstats = distil.profile_read(device=local)
     distil.profile_enable(timing=False, device=local)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
     entries = p.np_ * p.nb * p.nb * p.nt
-    value = world * entries * args.steps / (ms / 1e3)
+    value, all_entries, ms = job_throughput(entries, ms, args.steps, dist if world > 1 else None, dev)
+    ms_step = ms / args.steps
 
     # ---------------- end to end through the public API (host in, host out)
     C_host = torch.empty(C.shape, dtype=C.dtype).pin_memory()
@@ -343,10 +361,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     ms_e2e = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    e2e_value, _, ms_e2e = job_throughput(entries, ms_e2e, e2e_steps, dist if world > 1 else None, dev)
     h2d = v_h.nbytes + tau_h.nbytes + prof_h.nbytes
     d2h = C_host.numel() * 16 + lam_host.numel() * 16
 
@@ -369,7 +384,7 @@ def run_ours(args):
                        "mode": mode, "cfg_per_rank": 1, "parallelism": f"weak x{world} (cfg = rank)",
                        "l2": "inputs larger than L2 (v is %.1f GB)" % (v_h.nbytes / 1e9)},
             "tflops_algorithmic": flops["total"] * world / (ms_step / 1e3) / 1e12,
-            "e2e": {"value": world * entries * e2e_steps / (ms_e2e / 1e3), "unit": "entries/s",
+            "e2e": {"value": e2e_value, "unit": "entries/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in sorted(kstats.items(),
@@ -395,7 +410,7 @@ def run_ensemble(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     workers = min(32, os.cpu_count() or 1)
-    mine = [c for c in range(args.ncfg) if c % world == rank]
+    mine = shard_configs(args.ncfg, rank, world)
     log(f"ensemble of {args.ncfg} configurations, rank {rank} takes {mine}")
     host = [make_inputs(4, c, workers, args.nt) for c in mine]   # before any CUDA call
     log("inputs ready: v %.2f GB" % (sum(h[1].nbytes for h in host) / 1e9))
@@ -448,15 +463,7 @@ def run_ensemble(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     log(f"timed region: {ms / args.steps:.1f} ms per step")
-    tot = torch.tensor([float(entries), ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        ent = tot[:1].clone()
-        dist.all_reduce(ent, op=dist.ReduceOp.SUM)
-        mx = tot[1:].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        tot = torch.cat([ent, mx])
-    all_entries, ms_max = float(tot[0]), float(tot[1])
-    value = all_entries * args.steps / (ms_max / 1e3)
+    value, all_entries, ms_max = job_throughput(entries, ms, args.steps, dist if world > 1 else None, dev)
 
     # end to end: host inputs in, C and lambda out, through the same plan
     C_host = [torch.empty(c["C"].shape, dtype=c["C"].dtype).pin_memory() for c in cfgs]
@@ -475,7 +482,7 @@ def run_ensemble(args):
                 ch.copy_(c["C"], non_blocking=True)
     e1.record(s)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
+    e2e_value, _, ms_e2e = job_throughput(entries, e0.elapsed_time(e1), e2e_steps, dist if world > 1 else None, dev)
     h2d = sum(vp.nbytes + tp.nbytes + pp.nbytes for vp, tp, pp in pins)
     d2h = sum(ch.numel() * 16 for ch in C_host)
     out = None
@@ -491,7 +498,7 @@ def run_ensemble(args):
                        "ncfg": args.ncfg, "parallelism": f"weak x{world} (configuration c on rank c mod N)",
                        "graph": {"kernels_per_run": kernels, "variants": variants},
                        "l2": "inputs larger than L2"},
-            "e2e": {"value": all_entries * e2e_steps / (ms_e2e / 1e3), "unit": "entries/s",
+            "e2e": {"value": e2e_value, "unit": "entries/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(kernels * args.steps),
             "clocks": clk, "parity": None, "cpu_baseline": None,

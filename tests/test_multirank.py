@@ -1,0 +1,58 @@
+"""The multi-rank host logic of bench.py on CPU: two `gloo` ranks shard an
+ensemble of configurations (each configuration on exactly one rank, no
+data-path collective) and combine their timings into one whole-job
+throughput (entries summed over ranks, time = the slowest rank)."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, outdir):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        mine = bench.shard_configs(16, rank, world)
+        entries = 2016.0 * len(mine)            # C entries per step of this rank's configurations
+        ms = 100.0 + 50.0 * rank                # this rank's timed region
+        value, all_entries, ms_max = bench.job_throughput(entries, ms, 3, dist)
+        with open(os.path.join(outdir, f"rank{rank}.json"), "w") as f:
+            json.dump({"mine": mine, "value": value, "all": all_entries, "ms": ms_max}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_and_combine(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    shards = [set(r["mine"]) for r in res]
+    assert shards[0].isdisjoint(shards[1]) and shards[0] | shards[1] == set(range(16))
+    total = 2016.0 * 16
+    for r in res:   # every rank agrees on the whole-job numbers
+        assert r["all"] == total and r["ms"] == 150.0
+        assert r["value"] == pytest.approx(total * 3 / 0.150)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.shard_configs(5, 0, 1) == [0, 1, 2, 3, 4]
+    assert bench.shard_configs(5, 2, 4) == [2]
+    value, all_entries, ms = bench.job_throughput(100.0, 200.0, 4)
+    assert (all_entries, ms) == (100.0, 200.0) and value == pytest.approx(100 * 4 / 0.2)
