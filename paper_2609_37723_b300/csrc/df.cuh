@@ -57,6 +57,17 @@ __device__ __forceinline__ DF dot4(float a1, float b1, float a2, float b2, float
   const float lo = ((e1 + e2) + (e3 + e4)) + (s12.lo + s34.lo) + s.lo;
   return quick_two_sum(s.hi, lo);
 }
+// a + b (a - b) with one TwoSum on the leading parts and the trailing parts
+// added in FP32: error below 2^-44 (|a| + |b|), enough where the sum is
+// not the last word (it feeds products summed in double-float).
+__device__ __forceinline__ DF df_add_fast(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_sub_fast(DF a, DF b) {
+  const DF s = two_sum(a.hi, -b.hi);
+  return quick_two_sum(s.hi, s.lo + (a.lo - b.lo));
+}
 __device__ __forceinline__ DF df_neg(DF a) { return df_make(-a.hi, -a.lo); }
 __device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ DF df_mul(DF a, DF b) {

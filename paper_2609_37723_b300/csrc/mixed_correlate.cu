@@ -335,16 +335,29 @@ dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int 
     int ip, jp;
     pair_unrank(q, ip, jp);
     const long long o1 = ((long long)jp * nv + ip) * nv + k, o2 = ((long long)ip * nv + jp) * nv + k;
-    CDF w[NSRC];
-#pragma unroll
-    for (int c = 0; c < NSRC; ++c) w[c] = cdf_zero();
+    // d_t = V_{j'i'k} - V_{i'j'k} of the term's slot; the coefficients are
+    // -3, -2 (both on source 0) and +-1: w_0 = -(2 (d_0 + d_1) + d_0),
+    // w_c = coef_t d_t for the other sources (a sign, no product)
+    CDF d[NTERM];
 #pragma unroll
     for (int t = 0; t < NTERM; ++t) {
       const CDF* Vs = Va + dot_slot(t) * n3;
-      const CDF d = cdf_sub(ldg_cdf(Vs + o1), ldg_cdf(Vs + o2));
-      const float cf = (float)dot_coef(t);
-      const CDF wt = cdf_make(df_mul_f(d.re, cf), df_mul_f(d.im, cf));
-      w[dot_src(t)] = cdf_add(w[dot_src(t)], wt);
+      const CDF v1 = ldg_cdf(Vs + o1), v2 = ldg_cdf(Vs + o2);
+      d[t] = cdf_make(df_sub_fast(v1.re, v2.re), df_sub_fast(v1.im, v2.im));
+    }
+    static_assert(dot_coef(0) == -3.0 && dot_coef(1) == -2.0 && dot_src(0) == 0 && dot_src(1) == 0,
+                  "source-0 terms");
+    CDF w[NSRC];
+    {
+      const DF sr = df_add_fast(d[0].re, d[1].re), si = df_add_fast(d[0].im, d[1].im);
+      w[0] = cdf_make(df_neg(df_add_fast(df_make(2.f * sr.hi, 2.f * sr.lo), d[0].re)),
+                      df_neg(df_add_fast(df_make(2.f * si.hi, 2.f * si.lo), d[0].im)));
+    }
+#pragma unroll
+    for (int t = 2; t < NTERM; ++t) {
+      static_assert(dot_coef(2) == -1.0 && dot_coef(3) == 1.0 && dot_coef(4) == -1.0 && dot_coef(5) == 1.0,
+                    "unit coefficients");
+      w[dot_src(t)] = dot_coef(t) > 0 ? d[t] : cdf_make(df_neg(d[t].re), df_neg(d[t].im));
     }
 #pragma unroll
     for (int b = 0; b < MAXB; ++b) {
