@@ -365,6 +365,11 @@ def run_ours(args):
     h2d = v_h.nbytes + tau_h.nbytes + prof_h.nbytes
     d2h = C_host.numel() * 16 + lam_host.numel() * 16
 
+    # ---------------- the plain CUDA-core paths on the same GPU (rank 0), one timeslice
+    plain = None
+    if rank == 0 and not args.no_plain and mode not in ("fp64", "fp32"):
+        plain = plain_paths(distil, p, v_h, tau_h, prof, dev)
+
     # ---------------- parity of this run against the oracle on one slice (rank 0)
     out = None
     if rank == 0:
@@ -393,10 +398,38 @@ def run_ours(args):
             "clocks": clk,
             "parity": parity,
             "cpu_baseline": cpu,
+            "plain_paths": plain,
         }
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+def plain_paths(distil, p, v_h, tau_h, prof, dev):
+    """The plain FP32 and FP64 CUDA-core paths of the library on the same GPU
+    and inputs, on the first timeslice (all momenta, the source at t = 0 is
+    that timeslice): elementals + correlator, entries/s, for comparison with
+    the tensor-core mode."""
+    import torch
+    out = {}
+    for mode, cdt in (("fp32", np.complex64), ("fp64", np.complex128)):
+        v1 = torch.from_numpy(np.ascontiguousarray(v_h[:1].astype(cdt))).to(dev)
+        t1 = torch.from_numpy(np.ascontiguousarray(tau_h[:1].astype(cdt))).to(dev)
+        ms = []
+        for rep in range(2):   # the first run loads the kernels
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            phi = distil.elementals(v1, p.L, p.mom, mode)
+            C = distil.correlate(phi, phi[0], t1, prof, mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        entries = p.np_ * p.nb * p.nb
+        out[mode] = {"value": entries / (ms[-1] / 1e3), "unit": "entries/s", "ms": ms[-1],
+                     "sample": f"t = 0 slice: elementals of {p.np_} momenta + C_ab(0)"}
+        del v1, t1, phi, C
+    log("plain paths: " + ", ".join(f"{m} {r['value']:.1f} entries/s" for m, r in out.items()))
     return out
 
 
@@ -527,6 +560,19 @@ def kernel_cmacs(name, p):
     return table.get(name)
 
 
+# DRAM bytes (read + write) per launch from ncu's dram__bytes_* counters of
+# each tensor-core kernel family on the workload L32_Nt64_Nv128 (profiles/,
+# first two timeslices: the per-launch units are those of the full size).
+# Only valid for that workload and these kernels.
+TRAFFIC_L32_NV128 = {
+    "tc_gemm_elementals": 476.6e6 + 0.4e6,
+    "tc_gemm_step_i": 696.4e6 + 1939.9e6,
+    "tc_gemm_step_j": 625.1e6 + 353.5e6,
+    "tc_gemm_source": 78.5e6 + 442.0e6,
+    "dot": 1698.1e6 + 1.2e6,
+}
+
+
 def roofline(dom, kstats, p, mode, pk, steps):
     """Roofline of the dominant kernel family over the timed region."""
     if dom is None:
@@ -549,8 +595,9 @@ def roofline(dom, kstats, p, mode, pk, steps):
         bound = "tensor"
         note = (f"achieved = 8 x {prod} split products x complex MACs / event time: tensor flops the "
                 f"kernel must issue; peak = measured bf16 sustained (fp16 runs at the same rate)")
+    traffic = TRAFFIC_L32_NV128.get(dom) if (p.L, p.nv, p.np_, p.nb) == (32, 128, 5, 6) and mode == "fp16x6" else None
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if peak else None, "traffic": None, "per_unit": what,
+            "frac": (achieved / peak) if peak else None, "traffic": traffic, "per_unit": what,
             "launches": launches, "ms": ms, "note": note}
 
 
@@ -616,6 +663,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32/FP64 comparison")
     ap.add_argument("--ncfg", type=int, default=4,
                     help="workload 4: configurations in the ensemble (16 in full; each holds 3-6 GB of inputs)")
     ap.add_argument("--nt", type=int, default=0,
