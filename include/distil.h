@@ -208,7 +208,9 @@ int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* p
 
 /* Tensor-core kernel variant of each mode-contraction site of the mixed
  * correlator, variants[3] = {step i, step j, source}: 0 = one 128 x 128
- * tile per CTA, 1 = persistent CTAs with two 128 x 64 accumulator sets.
+ * tile per CTA, 1 = persistent CTAs with two 128 x 64 accumulator sets,
+ * 2 (step i only) = persistent with the whole-K A tile resident in shared
+ * memory (used when N_v <= 128, else variant 1).
  * Every variant gives identical results; only the speed differs.  The
  * defaults are {1, 0, 1}.  The library has no counterpart of this in the
  * paper: it is a property of this implementation. */

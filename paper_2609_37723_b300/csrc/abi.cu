@@ -59,7 +59,7 @@ int distil_create(int device, distil_ctx** out) {
   c->cc_minor = prop.minor;
   c->d_error = nullptr;
   c->prof = new Profiler();
-  c->tune[0] = 1;  // step i (K = N_v): persistent, epilogue overlapped
+  c->tune[0] = 1;  // step i (K = N_v): persistent, epilogue overlapped (2 measured slower at N_v = 128)
   c->tune[1] = 0;  // step j (K = 4 N_v): one 128 x 128 tile per CTA
   c->tune[2] = 1;  // source (K = N_v): persistent
   if (cudaMalloc(&c->d_error, sizeof(unsigned int) * 4) != cudaSuccess ||
@@ -203,7 +203,8 @@ int distil_set_tuning(distil_ctx* ctx, const int* variants) {
   g_err[0] = 0;
   DISTIL_CHECK_ARG(ctx != nullptr && variants != nullptr, "distil_set_tuning: null pointer");
   for (int i = 0; i < 3; ++i)
-    DISTIL_CHECK_ARG(variants[i] == 0 || variants[i] == 1, "distil_set_tuning: variant %d of site %d", variants[i], i);
+    DISTIL_CHECK_ARG(variants[i] == 0 || variants[i] == 1 || (i == 0 && variants[i] == 2),
+                     "distil_set_tuning: variant %d of site %d", variants[i], i);
   for (int i = 0; i < 3; ++i) ctx->tune[i] = variants[i];
   return DISTIL_OK;
 }

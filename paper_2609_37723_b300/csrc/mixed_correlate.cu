@@ -477,14 +477,19 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
 // names for this site: 0 = one 128 x 128 tile per CTA (wide MMAs, no
 // overlap of epilogue and MMAs), 1 = persistent CTAs with two 128 x 64
 // accumulator sets (the epilogue of one tile overlaps the MMAs of the
-// next).  Both accumulate every element over K in the same order, so they
-// give identical results.
+// next), 2 = the same with the whole-K A tile resident in shared memory
+// across the column tiles of a batch (K <= 128; else variant 1).  All
+// accumulate every element over K in the same order, so they give
+// identical results.
 enum GemmSite { SITE_STEP_I = 0, SITE_STEP_J = 1, SITE_SOURCE = 2 };
 template <bool BF16, int NPLA, int NPLB, class Epi>
 static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& A, const Planes& B,
                 const tc::GemmCfg& cfg, int batch, const Epi& epi, cudaStream_t s) {
   constexpr int KC = 16;
-  if (ctx->tune[site] == 1) {
+  constexpr int NKA = 8;  // resident A covers K <= 128
+  if (ctx->tune[site] == 2 && cfg.K <= NKA * KC && cfg.N > 32)
+    return tc::launch_gemm_ares<64, KC, NPLA, NPLB, NKA, BF16>(ctx, name, A, B, cfg, batch, epi, s);
+  if (ctx->tune[site] >= 1) {
     if (cfg.N > 32)
       return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(
           ctx, name, A, B, cfg, batch, epi, s);

@@ -61,11 +61,9 @@ int plan_sizes(const distil_batch_shape* sh, const distil_batch_cfg* cfgs, int n
 // The pipeline of one configuration (what the graph holds).
 int run_cfg(distil_ctx* ctx, const distil_batch_shape* sh, const distil_batch_cfg& cf, void* phi, void* ws,
             size_t ws_bytes, distil_stream s) {
-  const size_t T3 = (size_t)comb3(cf.nv);
   DISTIL_TRY(distil_elementals(ctx, cf.v, sh->L, sh->nt, cf.nv, sh->mom, sh->np, sh->mode, phi, ws, ws_bytes, s));
   DISTIL_TRY(distil_correlate(ctx, phi, phi, cf.tau, sh->nt, cf.nv, sh->np, cf.prof, sh->nb, 0, sh->mode, cf.C, ws,
                               ws_bytes, s));
-  (void)T3;
   if (cf.lambda) DISTIL_TRY(distil_gevp(ctx, cf.C, sh->np, sh->nb, sh->nt, sh->t0, cf.lambda, s));
   return DISTIL_OK;
 }
@@ -131,14 +129,21 @@ int distil_plan_create(distil_ctx* ctx, const distil_batch_shape* shape, const d
 
   const bool mixed = shape->mode != DISTIL_FP64 && shape->mode != DISTIL_FP32;
   if (autotune && mixed) {
-    double t[2][3];
-    for (int v = 0; v < 2; ++v) {
-      const int vv[3] = {v, v, v};
-      DISTIL_TRY(distil_set_tuning(ctx, vv));
+    // candidate vectors: every variant of every site appears (variant 2
+    // exists for step i only); each site keeps its fastest
+    static const int cand[3][3] = {{0, 0, 0}, {1, 1, 1}, {2, 1, 1}};
+    double t[3][3];
+    for (int v = 0; v < 3; ++v) {
+      DISTIL_TRY(distil_set_tuning(ctx, cand[v]));
       DISTIL_TRY(time_sites(ctx, shape, cfgs[0], phi, ws, wsb, stream, t[v]));
     }
     int best[3];
-    for (int k = 0; k < 3; ++k) best[k] = t[1][k] < t[0][k] ? 1 : 0;
+    for (int k = 0; k < 3; ++k) {
+      int bv = 0;
+      for (int v = 1; v < 3; ++v)
+        if (t[v][k] < t[bv][k]) bv = v;
+      best[k] = cand[bv][k];
+    }
     DISTIL_TRY(distil_set_tuning(ctx, best));
   }
 

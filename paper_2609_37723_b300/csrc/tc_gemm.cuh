@@ -502,5 +502,240 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// Persistent variant with the A operand resident in shared memory, for
+// short contractions (K <= NKA * KC) whose A tile serves many output tiles
+// (step i: one 128 x N_v tile of the tau blocks serves all N_v^2 / NT
+// column tiles of its batch).  CTA b walks a contiguous range of tiles (n
+// fastest), loads the whole-K A tile once per (m tile, batch) and streams
+// only B through the ring; TMEM holds two accumulator sets as in
+// tc_gemm_persistent_kernel.  Not for epilogues that skip tiles.
+//   afull   producer -> MMA: the resident A tile has landed
+//   afree   MMA -> producer: every MMA reading the resident A has completed
+template <int NT, int KC, int NPLA, int NPLB, int NKA, int STAGES, bool BF16, class Epi>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_ares_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                        GemmCfg cfg, Epi epi, int n_tiles, int m_tiles, int total_tiles) {
+  using G = TileGeom<NT, KC, NPLA, NPLB>;
+  static_assert(NT % 16 == 0 && NT >= 32 && 8 * NT <= 512, "two accumulator sets must fit TMEM");
+  static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
+  if (cfg.err && *(volatile unsigned*)cfg.err) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + NKA * G::A_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * G::B_STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* afull = tempty + 2;
+  uint64_t* afree = afull + 1;
+  uint64_t* done = afree + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint32_t* abort_flag = tslot + 1;
+  uint32_t* issued_s = tslot + 2;
+  uint32_t* aloads_s = tslot + 3;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (cfg.K + KC - 1) / KC;  // <= NKA, checked by the host
+  constexpr uint32_t SET = 4 * NT;
+  constexpr uint32_t TCOLS = 2 * SET;
+  const int per = (total_tiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int t_begin = (int)blockIdx.x * per;
+  const int t_end = min(total_tiles, t_begin + per);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);
+    }
+    mbar_init(afull, 1);
+    mbar_init(afree, 1);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    *issued_s = 0;
+    *aloads_s = 0;
+    fence_mbar_init();
+    tma_prefetch(&mapA);
+    tma_prefetch(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, TCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  volatile uint32_t* abort_v = abort_flag;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    uint32_t g = 0, reloads = 0;
+    int key = -1;
+    for (int t = t_begin; t < t_end && !*abort_v; ++t) {
+      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      if (rest != key) {
+        // the previous A tile is overwritten only after its last MMA completed
+        if (reloads > 0 && !mbar_wait(afree, (reloads - 1) & 1, cfg.err, TC_ERR_EMPTY_WAIT)) {
+          *abort_v = 1;
+          break;
+        }
+        const int ca = cfg.a.coord(batch);
+        mbar_arrive_expect_tx(afull, nk * G::A_STAGE);
+        for (int kb = 0; kb < nk; ++kb)
+          tma_load_4d(&mapA, afull, sA + kb * G::A_STAGE, kb * KC, m_tile * 128 + cfg.a.row_off, 0, ca);
+        ++reloads;
+        *(volatile uint32_t*)aloads_s = reloads;
+        key = rest;
+      }
+      const int cb = cfg.b.coord(batch);
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % STAGES);
+        const uint32_t ph = (g / STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT) || *abort_v) {
+          *abort_v = 1;
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], G::B_STAGE);
+        tma_load_4d(&mapB, &full[s], sB + s * G::B_STAGE, kb * KC, n_tile * NT + cfg.b.row_off, 0, cb);
+        *(volatile uint32_t*)issued_s = g + 1;
+      }
+      if (!ok) break;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    constexpr uint32_t id = idesc_f16(128, NT, BF16, false);
+    constexpr uint32_t idn = idesc_f16(128, NT, BF16, false, true);
+    constexpr MmaSchedule<NPLA, NPLB> S{};
+    uint32_t g = 0, it = 0, reloads = 0;
+    int key = -1;
+    for (int t = t_begin; t < t_end && !*abort_v; ++t) {
+      const int rest = t / n_tiles;
+      if (rest != key) {
+        if (!mbar_wait(afull, reloads & 1, cfg.err, TC_ERR_FULL_WAIT) || *abort_v) {
+          *abort_v = 1;
+          break;
+        }
+        ++reloads;
+        key = rest;
+      }
+      const uint32_t buf = it & 1, use = it >> 1;
+      if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT) || *abort_v) {
+        *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dset = tmem + buf * SET;
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % STAGES);
+        const uint32_t ph = (g / STAGES) & 1;
+        if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *abort_v) {
+          *abort_v = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da0 = smem_desc(smem_u32(sA + kb * G::A_STAGE), G::SWZ);
+        const uint64_t db0 = smem_desc(smem_u32(sB + s * G::B_STAGE), G::SWZ);
+        const uint32_t acc0 = kb ? 1u : 0u;
+#pragma unroll
+        for (int ks = 0; ks < KC / 16; ++ks) {
+#pragma unroll
+          for (int o = 0; o < S.n; ++o) {
+            const MmaOp op = S.ops[o];
+            const uint64_t da = da0 + (uint64_t)((op.ap * G::A_PLANE + ks * 32) >> 4);
+            const uint64_t db = db0 + (uint64_t)((op.bp * G::B_PLANE + ks * 32) >> 4);
+            const uint32_t accum = (ks > 0 || !op.first) ? 1u : acc0;
+            mma_f16(dset + (uint32_t)(op.dsel * NT), da, db, op.negb ? idn : id, accum);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      if (!ok) break;
+      mma_commit(&tfull[buf]);
+      ++it;
+      if (t + 1 >= t_end || (t + 1) / n_tiles != key) mma_commit(afree);  // last tile on this A
+    }
+    mma_commit(done);  // fires once every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    uint32_t it = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      const uint32_t buf = it & 1, use = it >> 1;
+      bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT);
+      ok = __all_sync(0xffffffffu, ok && !*abort_v);
+      if (!ok) {
+        if (lane == 0) *abort_v = 1;
+        break;
+      }
+      tc_fence_after();
+      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
+      typename Epi::State st;
+      epi.begin(st);
+      const int row = m_tile * 128 + q * 32 + lane;
+      const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
+      const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
+#pragma unroll 1
+      for (int c = half * (NT / 32); c < (half + 1) * (NT / 32); ++c) {
+        uint32_t r0[16], i0[16], r1[16], i1[16];
+        tmem_ld16(tl + c * 16, r0);
+        tmem_ld16(tl + NT + c * 16, i0);
+        tmem_ld16(tl + 2 * NT + c * 16, r1);
+        tmem_ld16(tl + 3 * NT + c * 16, i1);
+        tmem_wait_ld();
+        const int col0 = n_tile * NT + c * 16;
+        if (row < cfg.M) {
+          float re0[16], re1[16], im0[16], im1[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = col0 + e;
+            const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
+            const float f = pow2f(ea + eb - cfg.shift);
+            const float f1 = f * cfg.w1;
+            re0[e] = __uint_as_float(r0[e]) * f;
+            im0[e] = __uint_as_float(i0[e]) * f;
+            re1[e] = __uint_as_float(r1[e]) * f1;
+            im1[e] = __uint_as_float(i1[e]) * f1;
+          }
+          epi(st, batch, row, col0, re0, re1, im0, im1);
+        }
+      }
+      epi.end(st, batch);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      ++it;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (*abort_v) {
+      // drain: the last load of every ring stage and the last A tile
+      const uint32_t issued = *(volatile uint32_t*)issued_s;
+      for (uint32_t g = issued > (uint32_t)STAGES ? issued - STAGES : 0; g < issued; ++g) {
+        if (!mbar_wait(&full[g % STAGES], (g / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
+      }
+      const uint32_t al = *(volatile uint32_t*)aloads_s;
+      if (al > 0) mbar_wait(afull, (al - 1) & 1, cfg.err, TC_ERR_DRAIN);
+    }
+    mbar_wait(done, 0, cfg.err, TC_ERR_DRAIN);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
 }  // namespace tc
 }  // namespace distil

@@ -107,5 +107,50 @@ int launch_gemm_persistent(distil_ctx* ctx, const char* name, const Planes& A, c
   return DISTIL_OK;
 }
 
+// A-resident persistent launch: K <= NKA * KC; min(tiles, SMs) CTAs, each a
+// contiguous range of tiles.
+template <int NT, int KC, int NPLA, int NPLB, int NKA, bool BF16, class Epi>
+int launch_gemm_ares(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg,
+                     int batch, const Epi& epi, cudaStream_t s) {
+  using G = TileGeom<NT, KC, NPLA, NPLB>;
+  constexpr size_t room = 232448 - 1024 - 256 - (size_t)NKA * G::A_STAGE;
+  constexpr int ST0 = (int)(room / G::B_STAGE);
+  constexpr int STAGES = ST0 > 6 ? 6 : ST0;
+  static_assert(STAGES >= 2, "resident A leaves room for a two-stage B ring");
+  if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
+  if (cfg.K <= 0 || cfg.K > NKA * KC) {
+    set_error("%s: K=%d outside (0, %d] of the resident-A kernel", name, cfg.K, NKA * KC);
+    return DISTIL_EINVAL;
+  }
+  if (!products_match<NPLA, NPLB>(cfg)) {
+    set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
+    return DISTIL_EINVAL;
+  }
+  CUtensorMap ma, mb;
+  DISTIL_TRY(encode_planes(&ma, A, 128, KC, BF16));
+  DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
+  constexpr size_t smem = (size_t)NKA * G::A_STAGE + (size_t)STAGES * G::B_STAGE + 1024 + 256;
+  static_assert(smem <= 232448, "shared memory");
+  auto kern = tc_gemm_ares_kernel<NT, KC, NPLA, NPLB, NKA, STAGES, BF16, Epi>;
+  static bool attr = false;
+  if (!attr) {
+    DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const long long n_tiles = (cfg.N + NT - 1) / NT, m_tiles = (cfg.M + 127) / 128;
+  const long long total = n_tiles * m_tiles * batch;
+  if (total > 0x7fffffffLL) {
+    set_error("%s: too many tiles", name);
+    return DISTIL_EINVAL;
+  }
+  const int grid = (int)(total < ctx->sm_count ? total : ctx->sm_count);
+  {
+    Launch L(ctx, name, s);
+    kern<<<grid, TC_THREADS, smem, s>>>(ma, mb, cfg, epi, (int)n_tiles, (int)m_tiles, (int)total);
+  }
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
 }  // namespace tc
 }  // namespace distil

@@ -45,7 +45,8 @@ def test_plan_uneven_ensemble_mixed(cuda_lib, autotune):
     cfgs = device_cfgs(ens)
     plan = distil.Plan(4, 3, MOM, 2, 1, "fp16x6", cfgs, autotune=autotune)
     variants, kernels = plan.info()
-    assert all(v in (0, 1) for v in variants) and kernels > 10 * len(cfgs)
+    assert variants[0] in (0, 1, 2) and variants[1] in (0, 1) and variants[2] in (0, 1)
+    assert kernels > 10 * len(cfgs)
     assert distil.get_tuning() == variants
     plan.run()
     plan.stream.synchronize()
@@ -80,12 +81,13 @@ def test_tuning_variants_give_identical_results(cuda_lib):
     saved = distil.get_tuning()
     try:
         outs = []
-        for var in ([0, 0, 0], [1, 1, 1], [1, 0, 1]):
+        for var in ([0, 0, 0], [1, 1, 1], [1, 0, 1], [2, 0, 1], [2, 1, 0]):
             distil.set_tuning(var)
             outs.append(distil.correlate(phi, phi[0], tau, T(p.prof), "fp16x6").cpu().numpy())
     finally:
         distil.set_tuning(saved)
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
 
 
 def test_plan_fp64_matches_oracle(cuda_lib):
