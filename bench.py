@@ -8,12 +8,23 @@ of every (p, t).  The metric is C_ab(t) entries per second (N_p N_B^2 N_t
 entries per step per configuration); algorithmic TFLOP/s is reported beside
 it.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 3]
-                    [--mode fp16x3|bf16x6|bf16x3|fp32|fp64] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1..5]
+                    [--mode auto|fp16x6|fp16x3|bf16x6|bf16x3|fp32|fp64]
+                    [--impl ours|reference] [--ncfg K] [--nt NT]
+                    [--no-cpu-baseline] [--no-parity] [--no-plain]
+
+Default: workload 3 (L=32, N_t=64, N_v=128, 5 momenta, 6 profiles), mode
+fp16x6, 3 warm-up and 3 timed steps, plus the end-to-end leg (host inputs
+in, C out), a sampled parity check against the FP64 oracle, the oracle's own
+throughput on the host cores, and the plain FP32/FP64 paths on one
+timeslice.  Workload 4 runs an ensemble of --ncfg configurations with
+uneven N_v as one graph-captured plan.  --impl reference times the FP64
+oracle, one (t, p) slice per step.
 
 With N > 1 (launched by torch.distributed.run) every rank processes its own
-configuration (cfg = rank): weak scaling, no collective on the data path;
-the step time is the max over ranks.  Rank 0 prints one JSON line.
+configurations (configuration c on rank c mod N): weak scaling, no
+collective on the data path; entries are summed over ranks and the time is
+the slowest rank's.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
