@@ -257,6 +257,23 @@ def job_throughput(entries_local: float, ms_local: float, steps: int, dist=None,
     return all_entries * steps / (ms_max / 1e3), all_entries, ms_max
 
 
+def gather_C(C_local: dict, ncfg: int, dist=None):
+    """Rank 0 collects every configuration's correlation matrices after the
+    run (the one exchange of the sharded path; N_p N_B^2 N_t complex numbers
+    per configuration).  C_local maps configuration -> host tensor; returns
+    the list indexed by configuration on rank 0 (None elsewhere)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [C_local[c] for c in range(ncfg)]
+    parts = [None] * dist.get_world_size() if dist.get_rank() == 0 else None
+    dist.gather_object({c: t.numpy() for c, t in C_local.items()}, parts, dst=0)
+    if dist.get_rank() != 0:
+        return None
+    merged = {}
+    for part in parts:
+        merged.update(part)
+    return [merged[c] for c in range(ncfg)]
+
+
 # --------------------------------------------------------------------------- ours
 
 def peaks():
@@ -527,6 +544,9 @@ def run_ensemble(args):
     e1.record(s)
     torch.cuda.synchronize()
     e2e_value, _, ms_e2e = job_throughput(entries, e0.elapsed_time(e1), e2e_steps, dist if world > 1 else None, dev)
+    # every configuration's C on rank 0 (outside the timed regions)
+    gathered = gather_C({c: ch for c, ch in zip(mine, C_host)}, args.ncfg,
+                        dist if world > 1 else None)
     h2d = sum(vp.nbytes + tp.nbytes + pp.nbytes for vp, tp, pp in pins)
     d2h = sum(ch.numel() * 16 for ch in C_host)
     out = None
@@ -541,6 +561,7 @@ def run_ensemble(args):
                        "nv": [c["nv"] for c in cfgs], "np": p0.np_, "nb": p0.nb, "mode": mode,
                        "ncfg": args.ncfg, "parallelism": f"weak x{world} (configuration c on rank c mod N)",
                        "graph": {"kernels_per_run": kernels, "variants": variants},
+                       "C_gathered_on_rank0": len(gathered) if gathered is not None else 0,
                        "l2": "inputs larger than L2"},
             "e2e": {"value": e2e_value, "unit": "entries/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -30,8 +30,14 @@ def _rank_main(rank, world, port, outdir):
         entries = 2016.0 * len(mine)            # C entries per step of this rank's configurations
         ms = 100.0 + 50.0 * rank                # this rank's timed region
         value, all_entries, ms_max = bench.job_throughput(entries, ms, 3, dist)
+        # each rank's configurations' C (here filled with the configuration
+        # number) reach rank 0 in configuration order
+        import torch
+        local = {c: torch.full((2, 3, 3, 4), complex(c, -c), dtype=torch.complex128) for c in mine}
+        got = bench.gather_C(local, 16, dist)
+        gathered = None if got is None else [float(x.real.flat[0]) for x in got]
         with open(os.path.join(outdir, f"rank{rank}.json"), "w") as f:
-            json.dump({"mine": mine, "value": value, "all": all_entries, "ms": ms_max}, f)
+            json.dump({"mine": mine, "value": value, "all": all_entries, "ms": ms_max, "gathered": gathered}, f)
     finally:
         dist.destroy_process_group()
 
@@ -47,6 +53,7 @@ def test_two_gloo_ranks_shard_and_combine(tmp_path):
     for r in res:   # every rank agrees on the whole-job numbers
         assert r["all"] == total and r["ms"] == 150.0
         assert r["value"] == pytest.approx(total * 3 / 0.150)
+    assert res[0]["gathered"] == [float(c) for c in range(16)] and res[1]["gathered"] is None
 
 
 def test_single_rank_needs_no_process_group():
@@ -56,3 +63,6 @@ def test_single_rank_needs_no_process_group():
     assert bench.shard_configs(5, 2, 4) == [2]
     value, all_entries, ms = bench.job_throughput(100.0, 200.0, 4)
     assert (all_entries, ms) == (100.0, 200.0) and value == pytest.approx(100 * 4 / 0.2)
+    import torch
+    local = {c: torch.full((1,), float(c)) for c in (2, 0, 1)}
+    assert [float(t[0]) for t in bench.gather_C(local, 3)] == [0.0, 1.0, 2.0]
