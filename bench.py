@@ -423,6 +423,7 @@ def run_ours(args):
             "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in sorted(kstats.items(),
                                                                                   key=lambda kv: -kv[1][1])},
             "roofline": roof,
+            "kernel_rooflines": kernel_rooflines(kstats, p, mode, pk, args.steps),
             "clocks": clk,
             "parity": parity,
             "cpu_baseline": cpu,
@@ -571,6 +572,47 @@ def run_ensemble(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+def kernel_bytes(name, p):
+    """Algorithmic HBM bytes one step asks of the memory-side kernel
+    families: what they must read and write at least."""
+    n, nb, tp = p.nv, p.nb, p.nt * p.np_
+    P2 = n * (n - 1) // 2
+    table = {
+        # V (nb x 6 spin pairs x n^3) and X (nb x 5 x P2 x n), complex double-float, read once
+        "dot": ((96.0 * nb * n ** 3 + 80.0 * nb * P2 * n) * tp, "V + X per (t,p), 16 B each"),
+        # the cross-product planes written once: P2 x 3 V3 x 12 B per timeslice
+        "split_pairs": (12.0 * P2 * 3 * p.V3 * p.nt, "C(N_v,2) x 3 V3 x 12 B per t written"),
+    }
+    return table.get(name)
+
+
+def kernel_rooflines(kstats, p, mode, pk, steps):
+    """Every contraction kernel against the tensor peak (issued split
+    products) and the memory-side kernels against the measured HBM copy
+    bandwidth; achieved from the summed CUDA-event time over `steps` steps."""
+    out = []
+    if mode in ("fp64", "fp32"):
+        return out
+    prod = {"bf16x6": 6, "bf16x3": 3, "fp16x3": 3, "fp16x6": 6}[mode]
+    tpeak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
+    hpeak = pk.get("hbm_gbs") or 6400.0
+    for name, (launches, ms) in sorted(kstats.items(), key=lambda kv: -kv[1][1]):
+        if ms <= 0:
+            continue
+        c = kernel_cmacs(name, p)
+        if c is not None and name.startswith("tc_gemm"):
+            ach = 8.0 * prod * c[0] * steps / (ms / 1e3) / 1e12
+            out.append({"kernel": name, "bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
+                        "frac": ach / tpeak, "ms_per_step": ms / steps})
+            continue
+        b = kernel_bytes(name, p)
+        if b is not None:
+            ach = b[0] * steps / (ms / 1e3) / 1e9
+            out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hpeak, "unit": "GB/s",
+                        "frac": ach / hpeak, "ms_per_step": ms / steps, "per_unit": b[1]})
     return out
 
 
