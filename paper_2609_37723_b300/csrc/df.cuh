@@ -81,8 +81,6 @@ __device__ __forceinline__ DF df_mul_f(DF a, float b) {
   p.lo = __fmaf_rn(a.lo, b, p.lo);
   return quick_two_sum(p.hi, p.lo);
 }
-// exact scaling by a power of two
-__device__ __forceinline__ DF df_ldexp(DF a, int e) { return df_make(ldexpf(a.hi, e), ldexpf(a.lo, e)); }
 __device__ __forceinline__ DF df_from_double(double x) {
   const float hi = __double2float_rn(x);
   return df_make(hi, __double2float_rn(x - (double)hi));
@@ -91,13 +89,8 @@ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (do
 
 __device__ __forceinline__ CDF cdf_make(DF re, DF im) { CDF c; c.re = re; c.im = im; return c; }
 __device__ __forceinline__ CDF cdf_add(CDF a, CDF b) { return cdf_make(df_add(a.re, b.re), df_add(a.im, b.im)); }
-__device__ __forceinline__ CDF cdf_sub(CDF a, CDF b) { return cdf_make(df_sub(a.re, b.re), df_sub(a.im, b.im)); }
-__device__ __forceinline__ CDF cdf_mul(CDF a, CDF b) {
-  return cdf_make(df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re)));
-}
 __device__ __forceinline__ CDF cdf_scale(CDF a, DF s) { return cdf_make(df_mul(a.re, s), df_mul(a.im, s)); }
 __device__ __forceinline__ CDF cdf_conj(CDF a) { return cdf_make(a.re, df_neg(a.im)); }
-__device__ __forceinline__ CDF cdf_ldexp(CDF a, int e) { return cdf_make(df_ldexp(a.re, e), df_ldexp(a.im, e)); }
 __device__ __forceinline__ CDF cdf_zero() { return cdf_make(df_make(0.f, 0.f), df_make(0.f, 0.f)); }
 
 }  // namespace distil

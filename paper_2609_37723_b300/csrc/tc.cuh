@@ -39,9 +39,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
@@ -178,16 +175,6 @@ struct Piece<true> {
   static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
   static __device__ __forceinline__ float to(T h) { return __bfloat162float(h); }
 };
-
-// x = p[0] + p[1] + ... (each piece the rounding of what the earlier ones miss)
-template <bool BF16, int NP>
-__device__ __forceinline__ void split16(float x, typename Piece<BF16>::T (&p)[NP]) {
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    p[i] = Piece<BF16>::from(x);
-    x -= Piece<BF16>::to(p[i]);
-  }
-}
 
 }  // namespace tc
 }  // namespace distil
