@@ -99,3 +99,15 @@ def test_plan_rejects_bad_ensembles(L):
     assert L.distil_plan_create(None, ctypes.byref(shape), arr, 1, 0, None, 0, None, ctypes.byref(h)) == 1
     assert L.distil_plan_run(None, None) == 1
     L.distil_plan_destroy(None)
+
+
+def test_tuning_and_status_argument_checks(L):
+    """The tuning table, device-status and plan-info calls refuse null
+    handles without touching a device."""
+    arr = (ctypes.c_int * 3)(1, 0, 1)
+    assert L.distil_set_tuning(None, arr) == 1
+    assert L.distil_get_tuning(None, arr) == 1
+    code = ctypes.c_uint(7)
+    assert L.distil_device_status(None, 0, ctypes.byref(code)) == 1
+    assert b"null" in L.distil_last_error()
+    assert L.distil_plan_info(None, arr, None) == 1
