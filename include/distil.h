@@ -72,9 +72,10 @@ typedef enum {
  * correlation matrix and the GEVP are always c128.
  * Tensor-core modes split every operand row (power-of-two exponent of its
  * largest entry) into 16-bit pieces and accumulate in TMEM:
- *   FP16X6  fixed-point slices of 7 + 11 + 11 bits, 6 products; the leading
- *           product is integer-valued and sums exactly (about 2^-29 of the
- *           row maximum per GEMM).  The accurate mode.
+ *   FP16X6  fixed-point slices of 9 + 11 + 11 bits (10 + 11 + 11 in the
+ *           elementals), 6 products; the leading product is integer-valued
+ *           and sums exactly (about 2^-31 of the row maximum per GEMM).  The
+ *           accurate mode.
  *   BF16X6  fixed-point slices of 8 + 8 + 8 bits, 6 products (2^-24).
  *   BF16X3  fixed-point slices of 8 + 8 bits, 3 products (2^-16).
  *   FP16X3  floating pieces h + l (22 bits), 3 products; not exact: the
@@ -113,7 +114,8 @@ int distil_elementals_workspace(int L, int nt, int nv, int np, int mode, size_t*
  * triple of rank r, for t < nt and q < np.
  *   v    [nt][nv][L^3][3]   c128 (FP64) or c64 (other modes), device
  *   mom  [np][3] int32      integer momenta n, HOST pointer, read during the call
- *   phi  [nt][np][T3]       c128 (FP64) or c64, device, fully overwritten
+ *   phi  [nt][np][T3]       c64 in FP32 mode, c128 in FP64 and in every
+ *                           tensor-core mode; device, fully overwritten
  * Sizes: 1 <= L <= 256, nt >= 1, nv >= 1 (nv < 3 gives T3 = 0), np >= 1.
  * The elementals are the paper's Phi[p,t]_ijk before profiles (Sec. 2.1). */
 int distil_elementals(distil_ctx* ctx, const void* v, int L, int nt, int nv,
@@ -130,9 +132,11 @@ int distil_correlate_workspace(int nt, int nv, int np, int nb, int mode, size_t*
  *                 [Psi^(b)nu_{I'J'K'}(0) - Psi^(b)nu_{K'J'I'}(0)]^*
  * with Psi^(a)mu_{(alpha i)(beta j)(gamma k)} = g^(a)_i g^(a)_j g^(a)_k
  * Phi_ijk (C gamma_5)_{alpha beta} delta_{gamma mu}.
- *   phi_snk [nt][np][T3]      sink elementals at t (c128 FP64, else c64)
+ *   phi_snk [nt][np][T3]      sink elementals at t: c64 in FP32 mode, c128
+ *                             in FP64 and in every tensor-core mode
  *   phi_src [np][T3]          source elementals at t0 = 0 (same type)
- *   tau     [nt][4nv][4nv]    tau(t, t0) spin-major (same type)
+ *   tau     [nt][4nv][4nv]    tau(t, t0) spin-major: c128 in FP64 mode,
+ *                             else c64
  *   prof    [nb][nv] f64, or [nt][nb][nv] when prof_per_t != 0 (sink uses
  *           g[t], source g[0]); device pointer
  *   C       [np][nb][nb][nt]  c128, device, fully overwritten
@@ -186,14 +190,18 @@ int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, 
  * 16 MiB device array inside the library, held by every GPU that loads the
  * library until the process exits.  (The paper has no counterpart; this is
  * an interface convenience.)
- *  - Arguments and layouts as distil_correlate, without workspace; mode must
- *    be DISTIL_FP64 or DISTIL_FP32 (else DISTIL_EINVAL).
+ *  - Arguments, layouts and alignment rules as distil_correlate, without
+ *    workspace; mode must be DISTIL_FP64 or DISTIL_FP32 (else
+ *    DISTIL_EINVAL).  Misaligned arrays return DISTIL_EINVAL before any
+ *    launch.
  *  - Sizes needing more scratch than the array (FP64 about 352 N_B N_v^3
- *    bytes: e.g. N_v = 16 with N_B <= 16, N_v = 24 with N_B <= 3) return
- *    DISTIL_ENOMEM without touching the device.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *    bytes: N_v = 16 with N_B <= 11, N_v = 20 with N_B <= 5, N_v = 24 with
+ *    N_B <= 3; FP32 about half) return DISTIL_ENOMEM without touching the
+ *    device.
+ *  - Every call made outside stream capture looks up the array's device
+ *    address (cudaGetSymbolAddress) and caches it per device; a call made
+ *    while `stream` is being captured uses that cached address.  So make a
+ *    first call on each device before any stream capture.
  *  - Every call shares the one array, which keeps the last call's contents.
  *    Calls that overlap on the GPU (different streams, or several host
  *    threads) race on it: serialise them. */

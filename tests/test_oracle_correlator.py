@@ -232,6 +232,52 @@ def test_profile_is_diagonal_rescaling():
     np.testing.assert_allclose(a, b, atol=1e-14 * abs(b[0, 0]))
 
 
+def _per_t_case(seed, nv=4, nt=3, nb=3):
+    rng = np.random.default_rng(seed)
+    phs = rand_packed(rng, nv, (nt, 2))
+    ph0 = rand_packed(rng, nv, (2,))
+    tau = synth.complex_gaussian(rng, (nt, 4 * nv, 4 * nv))
+    g = rng.uniform(0.2, 1.0, size=(nb, nv))
+    return phs, ph0, tau, g
+
+
+def test_per_t_profiles_equal_reproduce_fixed_profiles():
+    """Profiles that depend on t (Sec. 2.1 writes g_i^(a)[t]) but are equal on
+    every timeslice give the t-independent correlation matrix."""
+    phs, ph0, tau, g = _per_t_case(61)
+    nt = tau.shape[0]
+    fixed = orc.correlator(phs, ph0, tau, g)
+    per_t = orc.correlator(phs, ph0, tau, np.stack([g] * nt), prof_per_t=True)
+    np.testing.assert_array_equal(per_t, fixed)
+
+
+def test_per_t_profiles_sink_at_t_source_at_t0():
+    """The sink elemental at t carries g[t], the source at t0 = 0 carries g[0]
+    (Sec. 2.1: Phi^(a)[p,t] = g[t] g[t] g[t] Phi[p,t]).  C is cubic in each
+    profile (one factor per quark), so with g[t] = c_a g for t >= 1 and
+    g[0] = g, row a of C(t >= 1) scales by c_a^3 (sink side only; were g[t]
+    used on both sides it would scale by c_a^3 c_b^3, were g[0] used for the
+    sink not at all), while C(t = 0), where sink and source both use g[0],
+    is unchanged.  Scaling the source profile g[0] instead scales the
+    columns of C(t >= 1) by c_b^3 and C(0) by c_a^3 c_b^3."""
+    phs, ph0, tau, g = _per_t_case(67)
+    nt, nb = tau.shape[0], g.shape[0]
+    c = np.array([2.0, 0.5, 1.5])
+    fixed = orc.correlator(phs, ph0, tau, g)
+    sink_scaled = np.stack([g] + [c[:, None] * g] * (nt - 1))
+    got = orc.correlator(phs, ph0, tau, sink_scaled, prof_per_t=True)
+    np.testing.assert_allclose(got[..., 0], fixed[..., 0], rtol=1e-13)
+    rows = (c ** 3)[None, :, None, None]
+    np.testing.assert_allclose(got[..., 1:], rows * fixed[..., 1:], rtol=1e-12)
+    src_scaled = np.stack([c[:, None] * g] + [g] * (nt - 1))
+    got = orc.correlator(phs, ph0, tau, src_scaled, prof_per_t=True)
+    cols = (c ** 3)[None, None, :, None]
+    np.testing.assert_allclose(got[..., 1:], cols * fixed[..., 1:], rtol=1e-12)
+    np.testing.assert_allclose(got[..., 0], (c ** 3)[None, :, None] * (c ** 3)[None, None, :] * fixed[..., 0],
+                               rtol=1e-12)
+    assert nb == len(c)
+
+
 # --------------------------------------------------------------------- GEVP
 
 def test_gevp_constructed_pencil():
