@@ -256,3 +256,53 @@ def gevp(C: np.ndarray, t0: int) -> np.ndarray:
             w = scipy.linalg.eigvals(C[p, :, :, t], A0)
             lam[p, t] = w[np.argsort(-np.abs(w), kind="stable")]
     return lam
+
+
+def _unit_phase(u: np.ndarray) -> np.ndarray:
+    """Scale a vector to unit 2-norm and rotate its phase so that its
+    largest-modulus component (the first of equal ones) is real positive."""
+    u = u / np.linalg.norm(u)
+    k = int(np.argmax(np.abs(u)))
+    return u * (np.conj(u[k]) / abs(u[k]))
+
+
+def gevp_vectors(C: np.ndarray, t0: int):
+    """Generalized eigenvalues and right eigenvectors of C(t) u = lambda C(t0) u
+    for every (p, t) (Sec. 2.1: the GEVP whose eigenvectors give the optimal
+    combination of the N_B profiled operators), by scipy.linalg.eig.
+    Returns lam[p][t][n] sorted by |lambda| descending and vecs[p][t][n][:],
+    each eigenvector of unit norm with its largest component real positive."""
+    npm, nb, _, nt = C.shape
+    lam = np.zeros((npm, nt, nb), dtype=np.complex128)
+    vecs = np.zeros((npm, nt, nb, nb), dtype=np.complex128)
+    for p in range(npm):
+        for t in range(nt):
+            w, u = scipy.linalg.eig(C[p, :, :, t], C[p, :, :, t0])
+            order = np.argsort(-np.abs(w), kind="stable")
+            lam[p, t] = w[order]
+            for n, col in enumerate(order):
+                vecs[p, t, n] = _unit_phase(u[:, col])
+    return lam, vecs
+
+
+def optimal_correlator(C: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Correlator of the optimal operators: C_n(t) = u_n^H C(t) u_n for the
+    eigenvectors u[p][n][:] of one GEVP (Sec. 2.1: the profiled operators
+    combined with the GEVP eigenvector weights).  Returns [p][n][t]."""
+    npm, nb, _, nt = C.shape
+    out = np.zeros((npm, nb, nt), dtype=np.complex128)
+    for p in range(npm):
+        for n in range(nb):
+            for t in range(nt):
+                out[p, n, t] = np.vdot(u[p, n], C[p, :, :, t] @ u[p, n])
+    return out
+
+
+def effective_mass(Cn: np.ndarray) -> np.ndarray:
+    """m_eff(t) = log(|C(t)| / |C(t+1)|) along the last axis (lattice units;
+    the moduli make it defined for the complex correlators of synthetic
+    inputs).  The last timeslice has no partner and gets NaN."""
+    a = np.abs(Cn)
+    out = np.full(Cn.shape, np.nan)
+    out[..., :-1] = np.log(a[..., :-1] / a[..., 1:])
+    return out

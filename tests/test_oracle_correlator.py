@@ -296,3 +296,66 @@ def test_gevp_constructed_pencil():
         expect = np.sort(lam ** (t - t0))[::-1]
         np.testing.assert_allclose(got[0, t], expect, rtol=1e-9)
         np.testing.assert_allclose(got[1, t], expect, rtol=1e-9)
+
+
+def _hermitian_pencil(seed, nb=5, nt=8):
+    """C(t) = B^H diag(lambda^t) B: the GEVP C(t) u = lambda C(t0) u has the
+    eigenvalues lambda_n^(t - t0) and the eigenvectors B^{-1} e_n (exactly)."""
+    rng = np.random.default_rng(seed)
+    lam = np.sort(rng.uniform(0.2, 0.95, nb))[::-1]
+    B = synth.complex_gaussian(rng, (nb, nb)) + 3 * np.eye(nb)
+    C = np.zeros((1, nb, nb, nt), dtype=np.complex128)
+    for t in range(nt):
+        C[0, :, :, t] = B.conj().T @ np.diag(lam ** t) @ B
+    return lam, B, C
+
+
+def test_gevp_vectors_constructed_pencil():
+    lam, B, C = _hermitian_pencil(71)
+    nb, nt, t0 = len(lam), C.shape[-1], 2
+    got_l, got_u = orc.gevp_vectors(C, t0)
+    Binv = np.linalg.inv(B)
+    for t in range(nt):
+        if t == t0:
+            continue      # every eigenvalue is 1 there: the vectors are not unique
+        order = np.argsort(-(lam ** (t - t0)), kind="stable")   # t < t0 reverses the order
+        np.testing.assert_allclose(got_l[0, t], (lam ** (t - t0))[order], rtol=1e-9)
+        for n in range(nb):
+            ref = Binv[:, order[n]] / np.linalg.norm(Binv[:, order[n]])
+            u = got_u[0, t, n]
+            assert abs(np.linalg.norm(u) - 1) < 1e-12
+            k = np.argmax(np.abs(u))
+            assert abs(u[k].imag) < 1e-14 and u[k].real > 0
+            assert abs(abs(np.vdot(ref, u)) - 1) < 1e-10     # the same vector up to a phase
+            # it solves the pencil it came from
+            r = C[0, :, :, t] @ u - got_l[0, t, n] * (C[0, :, :, t0] @ u)
+            assert np.linalg.norm(r) < 1e-10 * np.linalg.norm(C[0, :, :, t0])
+
+
+def test_optimal_correlator_and_effective_mass_closed_form():
+    """Projected with the exact eigenvectors u_n = B^{-1} e_n / |B^{-1} e_n|,
+    C_n(t) = lambda_n^t / |B^{-1} e_n|^2 and the effective mass is -log lambda_n
+    at every t."""
+    lam, B, C = _hermitian_pencil(73)
+    nb, nt = len(lam), C.shape[-1]
+    _, u = orc.gevp_vectors(C, 1)
+    Cn = orc.optimal_correlator(C, u[:, 4])
+    Binv = np.linalg.inv(B)
+    for n in range(nb):
+        expect = lam[n] ** np.arange(nt) / np.linalg.norm(Binv[:, n]) ** 2
+        np.testing.assert_allclose(Cn[0, n], expect, rtol=1e-9)
+    m = orc.effective_mass(Cn)
+    np.testing.assert_allclose(m[0, :, :-1], np.repeat(-np.log(lam)[:, None], nt - 1, axis=1), rtol=1e-9)
+    assert np.isnan(m[..., -1]).all()
+
+
+def test_optimal_correlator_is_phase_invariant_and_diagonalises():
+    """The projected correlator does not depend on the eigenvectors' phases,
+    and for this pencil the exact eigenvectors make C(t) diagonal."""
+    lam, B, C = _hermitian_pencil(79, nb=4)
+    _, u = orc.gevp_vectors(C, 1)
+    ref = u[:, 3]
+    rot = ref * np.exp(1j * np.array([0.3, -1.1, 2.0, 0.7]))[None, :, None]
+    np.testing.assert_allclose(orc.optimal_correlator(C, rot), orc.optimal_correlator(C, ref), rtol=1e-12)
+    off = ref[0].conj() @ C[0, :, :, 5] @ ref[0].T
+    assert np.abs(off - np.diag(np.diag(off))).max() < 1e-10 * np.abs(np.diag(off)).max()
