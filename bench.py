@@ -1,30 +1,30 @@
 #!/usr/bin/env python
 """Throughput of the distilled-nucleon hot path on B300.
 
-One step = the whole hot path for one gauge configuration of the workload:
-elementals Phi[t][p] for every timeslice and momentum, the N_B x N_B
-correlation matrix C_ab(t) for every (t, p) (source at t0 = 0) and the GEVP
-of every (p, t).  The metric is C_ab(t) entries per second (N_p N_B^2 N_t
-entries per step per configuration); algorithmic TFLOP/s is reported beside
-it.
+The metric is C_ab(t) entries per second; algorithmic TFLOP/s, the
+end-to-end rate through the public API (host inputs in, C out), the
+roofline of every kernel family and of the whole step, parity against
+stored FP64 oracle values, the oracle's own rate on the host cores and the
+plain FP32/FP64 CUDA-core paths are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1..5]
                     [--mode auto|fp16x6|fp16x3|bf16x6|bf16x3|fp32|fp64]
                     [--impl ours|reference] [--ncfg K] [--nt NT]
                     [--no-cpu-baseline] [--no-parity] [--no-plain]
 
-Default: workload 3 (L=32, N_t=64, N_v=128, 5 momenta, 6 profiles), mode
-fp16x6, 3 warm-up and 3 timed steps, plus the end-to-end leg (host inputs
-in, C out), a sampled parity check against the FP64 oracle, the oracle's own
-throughput on the host cores, and the plain FP32/FP64 paths on one
-timeslice.  Workload 4 runs an ensemble of --ncfg configurations with
-uneven N_v as one graph-captured plan.  --impl reference times the FP64
-oracle, one (t, p) slice per step.
+Default: workload 5 (L=48, N_t=96, N_v=256, 9 momenta, 8 profiles), mode
+fp16x6, one step = one sink timeslice of it (elementals of every momentum,
+C_ab(t) for every (p, a, b), the GEVP of C(t) with eigenvectors), 3 warm-up
+and 3 timed steps.  Workloads 1-3 time one whole configuration per step;
+workload 4 runs an ensemble of --ncfg configurations with uneven N_v as one
+graph-captured plan.  --impl reference times the FP64 oracle.
 
-With N > 1 (launched by torch.distributed.run) every rank processes its own
-configurations (configuration c on rank c mod N): weak scaling, no
-collective on the data path; entries are summed over ranks and the time is
-the slowest rank's.  Rank 0 prints one JSON line.
+--gpus N without a launcher starts N ranks under torch.distributed.run.
+With N ranks, workload 5 gives rank r the timeslices t = r mod N and
+workloads 1-4 the configurations c = r mod N: weak scaling, no collective
+on the data path; entries are summed over ranks and the time is the
+slowest rank's; C is gathered on rank 0 after the run.  Rank 0 prints one
+JSON line.
 """
 from __future__ import annotations
 
@@ -57,36 +57,39 @@ def log(msg: str):
 
 
 def _eig_worker(args):
-    cid, cfg, ts, shm_name, shape, dtype = args
+    cid, cfg, jobs, shm_name, shape, dtype = args
     from multiprocessing import shared_memory
     shm = shared_memory.SharedMemory(name=shm_name)
     out = np.ndarray(shape, dtype=dtype, buffer=shm.buf)
     p = synth.config(cid, cfg)
-    for t in ts:
-        out[t] = p.eigvecs(t)
+    for slot, t in jobs:
+        out[slot] = p.eigvecs(t)
     del out
     shm.close()
-    return len(ts)
+    return len(jobs)
 
 
-def make_inputs(cid: int, cfg: int, workers: int, nt: int = 0):
+def make_inputs(cid: int, cfg: int, workers: int, nt: int = 0, ts=None):
     """Host inputs of one configuration (numpy, identical bytes to the tests).
     Timeslices are drawn in parallel processes straight into shared memory.
     nt > 0 keeps only the first nt timeslices (a smaller case of the same
-    shapes, for profilers)."""
+    shapes, for profilers); ts, a list of timeslices, draws exactly those
+    (v[s] and tau[s] belong to timeslice ts[s])."""
     p = synth.config(cid, cfg)
     if nt > 0:
         p = dataclasses.replace(p, nt=min(p.nt, nt))
-    shape = (p.nt, p.nv, p.V3, 3)
+    ts = list(range(p.nt)) if ts is None else list(ts)
+    shape = (len(ts), p.nv, p.V3, 3)
     dtype = np.dtype(p.dtype)
-    if workers > 1 and p.nt > 1:
+    if workers > 1 and len(ts) > 1:
         import multiprocessing as mp
         from multiprocessing import shared_memory
         shm = shared_memory.SharedMemory(create=True, size=int(np.prod(shape)) * dtype.itemsize)
         for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ[var] = "1"   # one BLAS thread per worker process (inherited at spawn)
         try:
-            chunks = [list(range(w, p.nt, workers)) for w in range(workers)]
+            jobs = list(enumerate(ts))
+            chunks = [jobs[w::workers] for w in range(workers)]
             with mp.get_context("spawn").Pool(workers) as pool:
                 pool.map(_eig_worker, [(cid, cfg, c, shm.name, shape, dtype.str) for c in chunks if c])
             v = np.array(np.ndarray(shape, dtype=dtype, buffer=shm.buf))
@@ -94,8 +97,8 @@ def make_inputs(cid: int, cfg: int, workers: int, nt: int = 0):
             shm.close()
             shm.unlink()
     else:
-        v = p.all_eigvecs()
-    tau = p.all_perambulators()
+        v = np.stack([p.eigvecs(t) for t in ts])
+    tau = np.stack([p.perambulator(t) for t in ts])
     return p, v, tau
 
 
@@ -435,6 +438,324 @@ def run_ours(args):
     return out
 
 
+def shard_timeslices(nt: int, rank: int, world: int, count: int) -> list:
+    """The `count` sink timeslices rank `rank` processes, one per step: its
+    share t = rank, rank + world, ... of the N_t timeslices of a
+    configuration (every timeslice is independent given the source
+    elementals at t0 = 0, which each rank computes itself), repeated
+    cyclically when count exceeds the share."""
+    mine = [t for t in range(nt) if t % world == rank] or [rank % nt]
+    return [mine[i % len(mine)] for i in range(count)]
+
+
+def gather_columns(C_local, ts_local, dist=None):
+    """Rank 0 collects the C columns (timeslices) every rank computed after
+    the run: returns {t: C[..., t]} on rank 0 (None elsewhere)."""
+    cols = {int(t): C_local[..., t].copy() for t in sorted(set(ts_local))}
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return cols
+    parts = [None] * dist.get_world_size() if dist.get_rank() == 0 else None
+    dist.gather_object(cols, parts, dst=0)
+    if dist.get_rank() != 0:
+        return None
+    merged = {}
+    for part in parts:
+        merged.update(part)
+    return merged
+
+
+def elementals_issued_cmacs(p) -> float:
+    """Complex MACs the elementals GEMM issues for one timeslice (all
+    momenta): 128 x NT tiles of pairs (j-major) x (i, momentum) rows, NT =
+    128 (32 or 64 for fewer than 65 rows), over K = 3 V3 (each 4096-value
+    chunk padded to a multiple of 64), minus the tiles the kernel skips
+    because every i of the tile is >= every j."""
+    n, npm = p.nv, p.np_
+    pairs = [(j, k) for j in range(n) for k in range(j + 1, n)]
+    P2, R = len(pairs), n * npm
+    nt_tile = 128 if R > 64 else (64 if R > 32 else 32)
+    K = 3 * p.V3
+    kpad = sum(-(-min(4096, K - k0) // 64) * 64 for k0 in range(0, K, 4096))
+    tiles = 0
+    for m in range(-(-P2 // 128)):
+        jmax = pairs[min(m * 128 + 127, P2 - 1)][0]
+        for nn in range(-(-R // nt_tile)):
+            if (nn * nt_tile) // npm < jmax:
+                tiles += 1
+    return float(tiles) * 128 * nt_tile * kpad
+
+
+def golden_C(name: str):
+    """Stored FP64 oracle values of a workload (tests/golden, written by
+    make_oracle_golden.py from the oracle alone): {(t, p): C [nb][nb]}."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{name}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    out = {}
+    for smp in d["samples"]:
+        c = np.asarray(smp["C"], dtype=np.float64)
+        out[(smp["t"], smp["p"])] = c[..., 0] + 1j * c[..., 1]
+    return out
+
+
+def run_timeslices(args):
+    """One step = one sink timeslice t of the workload (default L = 48,
+    N_t = 96, N_v = 256, 9 momenta, 8 profiles): its elementals for every
+    momentum, the correlation matrix C_ab(t) for every (p, a, b) from the
+    source elementals at t0 = 0, and the GEVP of C(t) against C(t0) with
+    eigenvectors.  Every timeslice costs the same, so K steps are K / N_t of
+    the configuration: the source elementals are the sink elementals of
+    t = 0, computed once before the warm-up like every rank's own copy
+    (the GEVP reference C(t0) too).  With N ranks, rank r takes the
+    timeslices t = r mod N (weak scaling, no collective on the data path);
+    the C columns are gathered on rank 0 after the run."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cid = args.workload
+    p = synth.config(cid, 0)
+    t0_gevp = min(2, p.nt - 1)
+    steps_ts = shard_timeslices(p.nt, rank, world, args.warmup + args.steps)
+    setup_ts = [0, t0_gevp]
+    all_ts = setup_ts + steps_ts
+    uniq = sorted(set(all_ts))
+    workers = min(32, os.cpu_count() or 1)
+    log(f"generating {len(uniq)} timeslices of workload {cid} ({p.name}) with {workers} processes")
+    p, v_h, tau_h = make_inputs(cid, 0, workers, ts=uniq)   # before any CUDA call
+    slot = {t: i for i, t in enumerate(uniq)}
+    log(f"inputs ready: v {v_h.nbytes / 1e9:.2f} GB for {len(uniq)} timeslices")
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2609_37723_b300 import distil
+    mode = args.mode
+    if mode == "auto":
+        mode = next((m for m in ("fp16x6", "bf16x6") if distil.mode_available(m)), "fp32")
+    cdt = np.complex128 if mode == "fp64" else np.complex64
+    v_pin = torch.from_numpy(np.ascontiguousarray(v_h.astype(cdt, copy=False))).pin_memory()
+    del v_h
+    tau_pin = torch.from_numpy(np.ascontiguousarray(tau_h.astype(cdt, copy=False))).pin_memory()
+    prof_pin = torch.from_numpy(np.ascontiguousarray(p.prof)).pin_memory()
+    v = v_pin.to(dev)
+    tau = tau_pin.to(dev)
+    prof = prof_pin.to(dev)
+    stream = torch.cuda.current_stream()
+    tdt = torch.complex64 if mode == "fp32" else torch.complex128
+    T3 = p.T3
+    phi_src = torch.empty((1, p.np_, T3), dtype=tdt, device=dev)
+    phi_t = torch.empty((1, p.np_, T3), dtype=tdt, device=dev)
+    C = torch.zeros((p.np_, p.nb, p.nb, p.nt), dtype=torch.complex128, device=dev)
+    lam = torch.full((p.np_, p.nt, p.nb), complex("nan"), dtype=torch.complex128, device=dev)
+    vecs = torch.full((p.np_, p.nt, p.nb, p.nb), complex("nan"), dtype=torch.complex128, device=dev)
+    ws_e = distil.elementals_workspace(p.L, 1, p.nv, p.np_, mode)
+    ws_c = distil.correlate_workspace(1, p.nv, p.np_, p.nb, mode)
+    ws = torch.empty(max(ws_e, ws_c, 1), dtype=torch.uint8, device=dev)
+    log(f"device: v {v.numel() * v.element_size() / 1e9:.1f} GB, workspace {ws.numel() / 1e9:.1f} GB")
+
+    def step(t, vt, taut):
+        distil.elementals(vt, p.L, p.mom, mode, out=phi_t, workspace=ws)
+        distil.correlate_slice(phi_t[0], phi_src[0], taut, prof, prof, C, t, mode, workspace=ws)
+        distil.gevp_range(C, t0_gevp, t, 1, lam=lam, vecs=vecs)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # set-up: the source elementals (t0 = 0) and the GEVP reference C(t0)
+    distil.elementals(v[slot[0]:slot[0] + 1], p.L, p.mom, mode, out=phi_src, workspace=ws)
+    step(t0_gevp, v[slot[t0_gevp]:slot[t0_gevp] + 1], tau[slot[t0_gevp]])
+    torch.cuda.synchronize()
+    for i in range(args.warmup):
+        t = steps_ts[i]
+        step(t, v[slot[t]:slot[t] + 1], tau[slot[t]])
+        torch.cuda.synchronize()
+        log(f"warm-up step {i} (t = {t}) done")
+    timed_ts = steps_ts[args.warmup:]
+
+    # ---------------- timed region (device-resident inputs)
+    distil.profile_enable(timing=True, device=local)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for t in timed_ts:
+        step(t, v[slot[t]:slot[t] + 1], tau[slot[t]])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    log(f"timed region: {ms / args.steps:.1f} ms per step (one timeslice)")
+    kstats = distil.profile_read(device=local)
+    distil.profile_enable(timing=False, device=local)
+    entries = p.np_ * p.nb * p.nb          # one timeslice per step
+    value, all_entries, ms_max = job_throughput(entries, ms, args.steps, dist if world > 1 else None, dev)
+    ms_step = ms_max / args.steps
+
+    # ---------------- end to end: host v(t), tau(t) in, C and lambda out, every step
+    e2e_steps = max(1, min(args.steps, 3))
+    v_in = torch.empty_like(v[:1])
+    tau_in = torch.empty_like(tau[0])
+    C_host = torch.empty(C.shape, dtype=C.dtype).pin_memory()
+    lam_host = torch.empty(lam.shape, dtype=lam.dtype).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in timed_ts[:e2e_steps]:
+        v_in.copy_(v_pin[slot[t]:slot[t] + 1], non_blocking=True)
+        tau_in.copy_(tau_pin[slot[t]], non_blocking=True)
+        step(t, v_in, tau_in)
+        C_host.copy_(C, non_blocking=True)
+        lam_host.copy_(lam, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_value, _, _ = job_throughput(entries, e0.elapsed_time(e1), e2e_steps, dist if world > 1 else None, dev)
+    h2d = v_pin[0].numel() * v_pin.element_size() + tau_pin[0].numel() * tau_pin.element_size()
+    d2h = C_host.numel() * 16 + lam_host.numel() * 16
+
+    C_np = C.cpu().numpy()
+    gathered = gather_columns(C_np, [t0_gevp] + list(steps_ts), dist if world > 1 else None)
+    plain = None
+    if rank == 0 and not args.no_plain and mode not in ("fp64", "fp32"):
+        mid, late = p.nt // 2, p.nt - 1
+        plain = plain_paths_slices(distil, p, cid, [mid, late], prof, dev)
+    out = None
+    if rank == 0:
+        pk = peaks()
+        flops = algorithmic_flops(dataclasses.replace(p, nt=1))
+        dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+        p1 = dataclasses.replace(p, nt=1)
+        roof = roofline(dom, kstats, p1, mode, pk, args.steps)
+        launches = sum(l for l, _ in kstats.values())
+        gold = golden_C(p.name)
+        parity = None
+        if gold is not None and not args.no_parity:
+            errs = {}
+            for (t, q), ref in gold.items():
+                if t in gathered:
+                    got = gathered[t][q]
+                    e = np.abs(got - ref) / np.abs(ref)
+                    errs[f"t={t},p={q}"] = {"max_rel_err": float(e.max()),
+                                             "scaled_err": float(np.abs(got - ref).max() / np.abs(ref).max())}
+            parity = {"reference": "stored FP64 oracle values (tests/golden)", "slices": errs,
+                      "max_rel_err": max((x["max_rel_err"] for x in errs.values()), default=None)}
+        cpu = None if args.no_cpu_baseline else cpu_baseline_sampled(cid)
+        out = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(mode, mode + "(f32 accumulate)"),
+            "data": "synthetic (seeded orthonormal eigenvectors, Gaussian perambulators)",
+            "config": {"workload": p.name, "L": p.L, "nt": p.nt, "nv": p.nv, "np": p.np_, "nb": p.nb,
+                       "mode": mode, "step": "one sink timeslice: elementals (all momenta), C_ab(t) for all "
+                                             "(p, a, b), GEVP with eigenvectors",
+                       "parallelism": f"weak x{world} (timeslice t on rank t mod N)",
+                       "l2": "inputs larger than L2 (v(t) is %.2f GB per timeslice)"
+                             % (v[0].numel() * v.element_size() / 1e9)},
+            "tflops_algorithmic": flops["total"] * world / (ms_step / 1e3) / 1e12,
+            "e2e": {"value": e2e_value, "unit": "entries/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in sorted(kstats.items(),
+                                                                                  key=lambda kv: -kv[1][1])},
+            "roofline": roof,
+            "kernel_rooflines": kernel_rooflines(kstats, p1, mode, pk, args.steps),
+            "whole_step": whole_step_tensor(kstats, p1, mode, pk, args.steps, ms_step),
+            "clocks": clk,
+            "parity": parity,
+            "cpu_baseline": cpu,
+            "plain_paths": plain,
+            "gathered_timeslices": len(gathered) if gathered is not None else 0,
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def whole_step_tensor(kstats, p, mode, pk, steps, ms_step):
+    """Tensor flops the step's contraction kernels issue (elementals tiles
+    including the triangle-test waste, the three mode contractions) over the
+    whole step time, against the measured sustained bf16 peak."""
+    if mode in ("fp64", "fp32"):
+        return None
+    prod = {"bf16x6": 6, "bf16x3": 3, "fp16x3": 3, "fp16x6": 6}[mode]
+    n, nb, P2 = p.nv, p.nb, p.nv * (p.nv - 1) // 2
+    cm = elementals_issued_cmacs(p) * p.nt + (36.0 * nb * n ** 4 + 5.0 * nb * P2 * n * n) * p.nt * p.np_
+    flop = 8.0 * prod * cm
+    peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
+    ach = flop / (ms_step / 1e3) / 1e12
+    return {"issued_tflop_per_step": flop / 1e12, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "note": "issued split-product tensor flops of every contraction kernel / step time"}
+
+
+def plain_paths_slices(distil, p, cid, ts, prof, dev):
+    """The plain FP32 (all momenta) and FP64 (first momentum) CUDA-core paths
+    of the library on the same GPU, on the given sink timeslices with the
+    source at t0 = 0: elementals + C_ab(t), entries/s per timeslice."""
+    import torch
+    out = {}
+    _, v_h, tau_h = make_inputs(cid, 0, 1, ts=[0] + list(ts))
+    for mode, cdt, moms in (("fp32", np.complex64, p.mom), ("fp64", np.complex128, p.mom[:1])):
+        v1 = torch.from_numpy(np.ascontiguousarray(v_h.astype(cdt))).to(dev)
+        t1 = torch.from_numpy(np.ascontiguousarray(tau_h.astype(cdt))).to(dev)
+        npm = len(moms)
+        src = distil.elementals(v1[:1], p.L, moms, mode)
+        C = torch.zeros((npm, p.nb, p.nb, p.nt), dtype=torch.complex128, device=dev)
+        res = {}
+        for i, t in enumerate(ts):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            phi = distil.elementals(v1[i + 1:i + 2], p.L, moms, mode)
+            distil.correlate_slice(phi[0], src[0], t1[i + 1], prof, prof, C, t, mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            res[f"t={t}"] = {"value": npm * p.nb * p.nb / (ms / 1e3), "ms": ms}
+        out[mode] = {"unit": "entries/s", "momenta": npm, "timeslices": res,
+                     "sample": f"sink timeslices {list(ts)}, {npm} momenta, source at t0 = 0"}
+        del v1, t1, src, C
+    log("plain paths: " + "; ".join(f"{m} " + ", ".join(f"{k} {r['value']:.2f}" for k, r in o["timeslices"].items())
+                                    for m, o in out.items()))
+    return out
+
+
+def cpu_baseline_sampled(cid: int, m_el: int = 64, m_co: int = 96) -> dict:
+    """The FP64 oracle on a bounded sample of one (t, p = 0) slice of the
+    workload: the elementals of the first m_el modes (cost grows as N_v^3)
+    and the correlation matrix of the first m_co modes for one source profile
+    (cost grows as N_v^4 per profile), each scaled to the full N_v and N_B;
+    the slice's N_B^2 entries over the scaled time."""
+    from oracle import nucleon as orc
+    p = synth.config(cid, 0)
+    mom0 = p.mom[:1]
+    v1 = p.eigvecs(1).astype(np.complex128)
+    tau1 = p.perambulator(1).astype(np.complex128)
+    t_a = time.perf_counter()
+    orc.elementals_t(v1[:m_el], p.L, mom0)
+    el_s = time.perf_counter() - t_a
+    m = m_co
+    sub = np.concatenate([np.arange(a * p.nv, a * p.nv + m) for a in range(4)])
+    phi_m = orc.elementals_t(v1[:m], p.L, mom0)[0]
+    t_b = time.perf_counter()
+    orc.correlator_tp(phi_m, phi_m, tau1[np.ix_(sub, sub)], p.prof[:, :m], p.prof[:, :m], bs=[0])
+    co_s = time.perf_counter() - t_b
+    slice_s = el_s * (p.nv / m_el) ** 3 + co_s * (p.nv / m) ** 4 * p.nb
+    return {"value": p.nb * p.nb / slice_s, "unit": METRIC, "cores": OracleSlices.cores(), "kind": "oracle",
+            "sample": f"one (t=1, p=0) slice scaled from the oracle's elementals of {m_el} of {p.nv} modes "
+                      f"({el_s:.1f} s, x{(p.nv / m_el) ** 3:.0f}) and its correlator of {m} modes for one of "
+                      f"{p.nb} source profiles ({co_s:.1f} s, x{(p.nv / m) ** 4 * p.nb:.0f}); numpy FP64, "
+                      f"BLAS threads", "seconds": el_s + co_s, "slice_seconds_scaled": slice_s}
+
+
 def plain_paths(distil, p, v_h, tau_h, prof, dev):
     """The plain FP32 and FP64 CUDA-core paths of the library on the same GPU
     and inputs, on the first timeslice (all momenta, the source at t = 0 is
@@ -697,27 +1018,60 @@ def parity_slice(p, v_h, tau_h, C_gpu, mode):
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle as it stands on the host cores, one
-    (t, p = 0) slice of the same workload per step (untimed warm-up slices
-    first), entries/s = N_B^2 per slice / mean timed slice time."""
+    """The reference arm: the FP64 oracle as it stands on the host cores.
+    Workloads 1-4: one (t, p = 0) slice of the workload per step (untimed
+    warm-up slices first).  Workload 5 (one slice takes many minutes): each
+    step is the bounded sample of cpu_baseline_sampled on the slice
+    (t = 1, p = 0) -- the oracle's elementals of the first 64 modes and its
+    correlator of the first 96 modes for one source profile (cycling
+    through the profiles), scaled to the full slice by N_v^3 and N_B N_v^4.
+    entries/s = N_B^2 per slice / mean (scaled) slice time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     cid = 3 if args.workload == 4 else args.workload
-    o = OracleSlices(cid, args.nt)
-    p = o.p
     times = []
-    for i in range(args.warmup + args.steps):
-        t = 1 + i % (p.nt - 1) if p.nt > 1 else 0
-        dt = o.slice(t)
-        log(f"reference slice t={t}: {dt:.1f} s")
-        if i >= args.warmup:
-            times.append(dt)
+    if cid == 5:
+        from oracle import nucleon as orc
+        p = synth.config(cid, 0)
+        if args.nt > 0:
+            p = dataclasses.replace(p, nt=min(p.nt, args.nt))
+        m_el, m_co = 64, 96
+        mom0 = p.mom[:1]
+        v1 = p.eigvecs(1).astype(np.complex128)
+        tau1 = p.perambulator(1).astype(np.complex128)
+        sub = np.concatenate([np.arange(a * p.nv, a * p.nv + m_co) for a in range(4)])
+        tau_m = tau1[np.ix_(sub, sub)]
+        phi_m = orc.elementals_t(v1[:m_co], p.L, mom0)[0]       # input of the correlator sample (untimed)
+        g_m = np.ascontiguousarray(p.prof[:, :m_co])
+        for i in range(args.warmup + args.steps):
+            t_a = time.perf_counter()
+            orc.elementals_t(v1[:m_el], p.L, mom0)
+            el_s = time.perf_counter() - t_a
+            t_b = time.perf_counter()
+            orc.correlator_tp(phi_m, phi_m, tau_m, g_m, g_m, bs=[i % p.nb])
+            co_s = time.perf_counter() - t_b
+            dt = el_s * (p.nv / m_el) ** 3 + co_s * (p.nv / m_co) ** 4 * p.nb
+            log(f"reference sample {i}: {el_s + co_s:.1f} s, scaled slice {dt:.0f} s")
+            if i >= args.warmup:
+                times.append(dt)
+        sample = (f"{args.steps} timed samples after {args.warmup} untimed, each the (t=1, p=0) slice scaled from "
+                  f"the oracle's elementals of {m_el} of {p.nv} modes (x{(p.nv / m_el) ** 3:.0f}) and its "
+                  f"correlator of {m_co} modes for one of {p.nb} source profiles (x{(p.nv / m_co) ** 4 * p.nb:.0f})")
+    else:
+        o = OracleSlices(cid, args.nt)
+        p = o.p
+        for i in range(args.warmup + args.steps):
+            t = 1 + i % (p.nt - 1) if p.nt > 1 else 0
+            dt = o.slice(t)
+            log(f"reference slice t={t}: {dt:.1f} s")
+            if i >= args.warmup:
+                times.append(dt)
+        sample = (f"{args.steps} timed (t, p=0) slices after {args.warmup} untimed: sink elementals + "
+                  f"C_ab(t) each, plus 1/N_t of the t=0 source elementals ({o.src_s:.1f} s)")
     ms = 1e3 * statistics.mean(times)
     val = p.nb * p.nb / (ms / 1e3)
-    cb = {"value": val, "unit": METRIC, "cores": o.cores(), "kind": "oracle",
-          "sample": f"{args.steps} timed (t, p=0) slices after {args.warmup} untimed: sink elementals + "
-                    f"C_ab(t) each, plus 1/N_t of the t=0 source elementals ({o.src_s:.1f} s)"}
+    cb = {"value": val, "unit": METRIC, "cores": OracleSlices.cores(), "kind": "oracle", "sample": sample}
     return {"metric": METRIC, "value": val, "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -726,12 +1080,26 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def spawn_ranks(n: int) -> int:
+    """bench.py --gpus N run without a launcher: start N ranks of this script
+    under torch.distributed.run on this node (127.0.0.1) and return its exit
+    status."""
+    import socket
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--mode", default="auto")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -743,10 +1111,16 @@ def main():
     ap.add_argument("--nt", type=int, default=0,
                     help="keep only the first NT timeslices (profiling a smaller case; not a bench number)")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args.gpus))
+    if args.warmup < 3 and args.impl == "ours" and args.workload == 5:
+        ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload == 4:
         out = run_ensemble(args)
+    elif args.workload == 5:
+        out = run_timeslices(args)
     else:
         out = run_ours(args)
     if out is not None:

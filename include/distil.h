@@ -146,6 +146,24 @@ int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src,
                      const double* prof, int nb, int prof_per_t, int mode,
                      void* C, void* workspace, size_t ws_bytes, distil_stream stream);
 
+/* One sink timeslice of the correlation matrix, for workloads processed
+ * one timeslice at a time (the eigenvectors and perambulators of one t at
+ * a time on the device).  Computes C[q][a][b][t] for every q, a, b of an
+ * array with nt timeslices and leaves the other columns of C untouched;
+ * the arithmetic is the one of distil_correlate for that timeslice.
+ *   phi_snk_t [np][T3]      sink elementals at timeslice t (types as above)
+ *   phi_src   [np][T3]      source elementals at t0 = 0
+ *   tau_t     [4nv][4nv]    tau(t, t0)
+ *   prof_snk  [nb][nv] f64  sink profiles g^(a)[t] (Sec. 2.1: g_i^(a)[t])
+ *   prof_src  [nb][nv] f64  source profiles g^(b)[t0]
+ *   C         [np][nb][nb][nt] c128, column t written
+ * Workspace: distil_correlate_workspace(1, nv, np, nb, mode).
+ * Sizes: 0 <= t < nt, nv, np >= 1, 1 <= nb <= 16. */
+int distil_correlate_slice(distil_ctx* ctx, const void* phi_snk_t, const void* phi_src,
+                           const void* tau_t, int nv, int np, const double* prof_snk,
+                           const double* prof_src, int nb, int mode, void* C, int nt, int t,
+                           void* workspace, size_t ws_bytes, distil_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* GEVP                                                                */
 /* ------------------------------------------------------------------ */
@@ -160,6 +178,33 @@ int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src,
  * Sizes: 1 <= nb <= 16, 0 <= t0 < nt. */
 int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0,
                 void* lambda, distil_stream stream);
+
+/* The GEVP of distil_gevp for the timeslices t_begin <= t < t_begin +
+ * t_count only (lambda entries of other timeslices untouched), and
+ * optionally its right eigenvectors (Sec. 2.1: the GEVP whose eigenvectors
+ * combine the N_B profiled operators into the optimal one):
+ *   vecs [np][nt][nb][nb] c128 device or NULL: vecs[q][t][n][:] solves
+ *        C(t) u = lambda_n C(t0) u for the n-th eigenvalue of lambda[q][t],
+ *        scaled to unit 2-norm with its largest-modulus component real and
+ *        positive (NaN where lambda is NaN).
+ * Eigenvectors come from the complex Schur form of C(t0)^{-1} C(t) (the
+ * accumulated Householder and Givens transformations) and back substitution.
+ * Sizes: as distil_gevp, 0 <= t_begin, t_begin + t_count <= nt. */
+int distil_gevp_range(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0,
+                      int t_begin, int t_count, void* lambda, void* vecs, distil_stream stream);
+
+/* Correlators of the optimal operators (Sec. 2.1: the N_B profiled
+ * operators combined with the weights of a GEVP eigenvector, the optimal
+ * profile combination for each state) and their effective masses:
+ *   copt[q][n][t] = u^H C[q][:][:][t] u,  u = vecs[q][td][n][:]
+ *   meff[q][n][t] = log(|copt[q][n][t]| / |copt[q][n][t+1]|), NaN at t = nt-1
+ *   C    [np][nb][nb][nt] c128 device;  vecs [np][nt][nb][nb] c128 device,
+ *        as written by distil_gevp_range (its timeslice td is used)
+ *   copt [np][nb][nt] c128 device;  meff [np][nb][nt] f64 device or NULL.
+ * The moduli make the effective mass defined for complex correlators.
+ * Sizes: 1 <= nb <= 16, 0 <= td < nt. */
+int distil_optimal(distil_ctx* ctx, const void* C, int np, int nb, int nt, const void* vecs,
+                   int td, void* copt, double* meff, distil_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* Split-precision complex GEMM (the tensor-core engine on its own)    */

@@ -22,7 +22,10 @@ void set_error(const char* fmt, ...) {
 }
 const char* get_error() { return g_err; }
 
-int gevp_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, void* lambda, cudaStream_t s);
+int gevp_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, int t_begin, int t_count,
+                void* lambda, void* vecs, cudaStream_t s);
+int optimal_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, const void* vecs, int td, void* copt,
+                   double* meff, cudaStream_t s);
 
 Profiler& profiler(distil_ctx* ctx) { return *ctx->prof; }
 
@@ -151,10 +154,40 @@ int distil_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, 
     return DISTIL_ENOMEM;
   }
   if (is_mixed(mode))
-    return correlate_mixed(ctx, mode, phi_snk, phi_src, tau, nt, nv, np, prof, nb, prof_per_t, C, workspace,
-                           ws_bytes, s);
-  return correlate_plain(ctx, mode == DISTIL_FP64, phi_snk, phi_src, tau, nt, nv, np, prof, nb, prof_per_t, C,
-                         workspace, ws_bytes, s);
+    return correlate_mixed(ctx, mode, phi_snk, phi_src, tau, nt, nv, np, prof, prof, prof_per_t, nb, C, nt, 0,
+                           workspace, ws_bytes, s);
+  return correlate_plain(ctx, mode == DISTIL_FP64, phi_snk, phi_src, tau, nt, nv, np, prof, prof, prof_per_t, nb, C,
+                         nt, 0, workspace, ws_bytes, s);
+}
+
+int distil_correlate_slice(distil_ctx* ctx, const void* phi_snk_t, const void* phi_src, const void* tau_t, int nv,
+                           int np, const double* prof_snk, const double* prof_src, int nb, int mode, void* C, int nt,
+                           int t, void* workspace, size_t ws_bytes, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(valid_mode(mode), "distil_correlate_slice: bad mode %d", mode);
+  DISTIL_CHECK_ARG(nv >= 1 && np >= 1 && nt >= 1, "distil_correlate_slice: nv, np, nt must be >= 1");
+  DISTIL_CHECK_ARG(t >= 0 && t < nt, "distil_correlate_slice: t=%d outside [0,%d)", t, nt);
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_correlate_slice: nb=%d outside [1,16]", nb);
+  DISTIL_CHECK_ARG(tau_t && prof_snk && prof_src && C && ((phi_snk_t && phi_src) || comb3(nv) == 0),
+                   "distil_correlate_slice: null pointer");
+  const size_t phi_al = mode == DISTIL_FP32 ? 8 : 16;
+  DISTIL_CHECK_ARG(aligned(phi_snk_t, phi_al) && aligned(phi_src, phi_al) &&
+                       aligned(tau_t, mode == DISTIL_FP64 ? 16 : 8) && aligned(prof_snk, 8) &&
+                       aligned(prof_src, 8) && aligned(C, 16) && aligned(workspace, 256),
+                   "distil_correlate_slice: misaligned pointer (arrays to their element, workspace to 256 bytes)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  size_t need = 0;
+  distil_correlate_workspace(1, nv, np, nb, mode, &need);
+  if (nv >= 3 && (ws_bytes < need || !workspace)) {
+    set_error("distil_correlate_slice: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  if (is_mixed(mode))
+    return correlate_mixed(ctx, mode, phi_snk_t, phi_src, tau_t, 1, nv, np, prof_snk, prof_src, 0, nb, C, nt, t,
+                           workspace, ws_bytes, s);
+  return correlate_plain(ctx, mode == DISTIL_FP64, phi_snk_t, phi_src, tau_t, 1, nv, np, prof_snk, prof_src, 0, nb,
+                         C, nt, t, workspace, ws_bytes, s);
 }
 
 int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, void* lambda,
@@ -165,7 +198,35 @@ int distil_gevp(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, 
   DISTIL_CHECK_ARG(np >= 1 && nt >= 1, "distil_gevp: np, nt must be >= 1");
   DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_gevp: nb=%d outside [1,16]", nb);
   DISTIL_CHECK_ARG(t0 >= 0 && t0 < nt, "distil_gevp: t0=%d outside [0,%d)", t0, nt);
-  return gevp_launch(ctx, C, np, nb, nt, t0, lambda, reinterpret_cast<cudaStream_t>(stream));
+  DISTIL_CHECK_ARG(aligned(C, 16) && aligned(lambda, 16), "distil_gevp: misaligned pointer");
+  return gevp_launch(ctx, C, np, nb, nt, t0, 0, nt, lambda, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_gevp_range(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, int t_begin, int t_count,
+                      void* lambda, void* vecs, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(C && lambda, "distil_gevp_range: null pointer");
+  DISTIL_CHECK_ARG(np >= 1 && nt >= 1, "distil_gevp_range: np, nt must be >= 1");
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_gevp_range: nb=%d outside [1,16]", nb);
+  DISTIL_CHECK_ARG(t0 >= 0 && t0 < nt, "distil_gevp_range: t0=%d outside [0,%d)", t0, nt);
+  DISTIL_CHECK_ARG(t_begin >= 0 && t_count >= 0 && t_begin + t_count <= nt,
+                   "distil_gevp_range: timeslices [%d,%d) outside [0,%d)", t_begin, t_begin + t_count, nt);
+  DISTIL_CHECK_ARG(aligned(C, 16) && aligned(lambda, 16) && aligned(vecs, 16), "distil_gevp_range: misaligned pointer");
+  return gevp_launch(ctx, C, np, nb, nt, t0, t_begin, t_count, lambda, vecs, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_optimal(distil_ctx* ctx, const void* C, int np, int nb, int nt, const void* vecs, int td, void* copt,
+                   double* meff, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(C && vecs && copt, "distil_optimal: null pointer");
+  DISTIL_CHECK_ARG(np >= 1 && nt >= 1, "distil_optimal: np, nt must be >= 1");
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= 16, "distil_optimal: nb=%d outside [1,16]", nb);
+  DISTIL_CHECK_ARG(td >= 0 && td < nt, "distil_optimal: td=%d outside [0,%d)", td, nt);
+  DISTIL_CHECK_ARG(aligned(C, 16) && aligned(vecs, 16) && aligned(copt, 16) && aligned(meff, 8),
+                   "distil_optimal: misaligned pointer");
+  return optimal_launch(ctx, C, np, nb, nt, vecs, td, copt, meff, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int distil_cgemm_workspace(int M, int N, int K, int batch, int mode, size_t* bytes) {

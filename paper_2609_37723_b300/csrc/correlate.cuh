@@ -43,9 +43,20 @@ __host__ __device__ constexpr double dot_coef(int t) {
   return t == 0 ? -3.0 : t == 1 ? -2.0 : (t == 2 || t == 4) ? -1.0 : 1.0;
 }
 
+// Both paths compute C for the call's nt sink timeslices t into
+// C[q][a][b][c_t0 + t] of an array with c_nt timeslices (other columns are
+// not touched).  Sink timeslice t uses the profiles prof_snk (+ t nb nv when
+// prof_per_t), the source prof_src.
 int correlate_plain(distil_ctx* ctx, int fp64, const void* phi_snk, const void* phi_src, const void* tau,
-                    int nt, int nv, int np, const double* prof, int nb, int prof_per_t,
-                    void* C, void* ws, size_t ws_bytes, cudaStream_t s);
+                    int nt, int nv, int np, const double* prof_snk, const double* prof_src, int prof_per_t, int nb,
+                    void* C, int c_nt, int c_t0, void* ws, size_t ws_bytes, cudaStream_t s);
+
+// Zero the columns [c_t0, c_t0 + nt) of `rows` rows of c_nt complex128 values.
+inline int zero_c_columns(void* C, long long rows, int c_nt, int c_t0, int nt, cudaStream_t s) {
+  const size_t e = sizeof(double) * 2;
+  DISTIL_CUDA(cudaMemset2DAsync(static_cast<char*>(C) + e * c_t0, e * c_nt, 0, e * nt, (size_t)rows, s));
+  return DISTIL_OK;
+}
 size_t correlate_plain_workspace(int fp64, int nv, int nb);
 
 }  // namespace distil

@@ -194,18 +194,18 @@ static int run_tp(distil_ctx* ctx, const Cx<T>* phi_snk_tp, const Cx<T>* phi_src
 }
 
 int correlate_plain(distil_ctx* ctx, int fp64, const void* phi_snk, const void* phi_src, const void* tau,
-                    int nt, int nv, int np, const double* prof, int nb, int prof_per_t,
-                    void* C, void* ws, size_t ws_bytes, cudaStream_t s) {
-  DISTIL_CUDA(cudaMemsetAsync(C, 0, sizeof(Cx<double>) * (size_t)np * nb * nb * nt, s));
+                    int nt, int nv, int np, const double* prof_snk, const double* prof_src, int prof_per_t, int nb,
+                    void* C, int c_nt, int c_t0, void* ws, size_t ws_bytes, cudaStream_t s) {
+  DISTIL_TRY(zero_c_columns(C, np * nb * nb, c_nt, c_t0, nt, s));
   if (nv < 3) return DISTIL_OK;
   const long long T3 = comb3(nv), n4 = 4LL * nv;
   Arena ar(ws, ws_bytes);
   Cx<double>* Cd = reinterpret_cast<Cx<double>*>(C);
   for (int t = 0; t < nt; ++t) {
-    const double* g_snk = prof + (prof_per_t ? (long long)t * nb * nv : 0);
-    const double* g_src = prof;
+    const double* g_snk = prof_snk + (prof_per_t ? (long long)t * nb * nv : 0);
+    const double* g_src = prof_src;
     for (int q = 0; q < np; ++q) {
-      Cx<double>* Cq = Cd + (long long)q * nb * nb * nt + t;
+      Cx<double>* Cq = Cd + (long long)q * nb * nb * c_nt + c_t0 + t;
       if (fp64) {
         Arena a2 = ar;
         PlainWs<double> w = carve<double>(a2, nv, nb);
@@ -213,7 +213,7 @@ int correlate_plain(distil_ctx* ctx, int fp64, const void* phi_snk, const void* 
         DISTIL_TRY(run_tp<double>(ctx, (const Cx<double>*)phi_snk + ((long long)t * np + q) * T3,
                                   (const Cx<double>*)phi_src + (long long)q * T3,
                                   (const Cx<double>*)tau + (long long)t * n4 * n4, g_snk, g_src, nv, nb, w,
-                                  Cq, (long long)nb * nt, nt, s));
+                                  Cq, (long long)nb * c_nt, c_nt, s));
       } else {
         Arena a2 = ar;
         PlainWs<float> w = carve<float>(a2, nv, nb);
@@ -221,7 +221,7 @@ int correlate_plain(distil_ctx* ctx, int fp64, const void* phi_snk, const void* 
         DISTIL_TRY(run_tp<float>(ctx, (const Cx<float>*)phi_snk + ((long long)t * np + q) * T3,
                                  (const Cx<float>*)phi_src + (long long)q * T3,
                                  (const Cx<float>*)tau + (long long)t * n4 * n4, g_snk, g_src, nv, nb, w,
-                                 Cq, (long long)nb * nt, nt, s));
+                                 Cq, (long long)nb * c_nt, c_nt, s));
       }
     }
   }

@@ -595,9 +595,9 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
 int mixed_mode_built(int mode) { return is_mixed(mode) ? 1 : 0; }
 
 int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* phi_src, const void* tau, int nt,
-                    int nv, int np, const double* prof, int nb, int prof_per_t, void* C, void* ws,
-                    size_t ws_bytes, cudaStream_t s) {
-  DISTIL_CUDA(cudaMemsetAsync(C, 0, sizeof(Cx<double>) * (size_t)np * nb * nb * nt, s));
+                    int nv, int np, const double* prof_snk, const double* prof_src, int prof_per_t, int nb, void* C,
+                    int c_nt, int c_t0, void* ws, size_t ws_bytes, cudaStream_t s) {
+  DISTIL_TRY(zero_c_columns(C, (long long)np * nb * nb, c_nt, c_t0, nt, s));
   if (nv < 3) return DISTIL_OK;
   const Scheme sch = scheme_of(mode);
   Arena ar(ws, ws_bytes);
@@ -608,12 +608,14 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   }
   const long long T3 = comb3(nv), n4 = 4LL * nv;
   const long long nprof = (prof_per_t ? (long long)nt : 1) * nb * nv;
+  DF* g_src = w.g + (long long)nt * nb * nv;  // the source profiles follow the sink blocks
   {
     Launch L(ctx, "normalise", s);
     c64_exp_kernel<<<nt, 256, 0, s>>>((const float2*)tau, n4 * n4, w.etau);
     c128_exp_kernel<<<nt * np, 256, 0, s>>>((const double2*)phi_snk, T3, w.esnk);
     c128_exp_kernel<<<np, 256, 0, s>>>((const double2*)phi_src, T3, w.esrc);
-    prof_to_df_kernel<<<nblk(nprof), 256, 0, s>>>(prof, nprof, w.g);
+    prof_to_df_kernel<<<nblk(nprof), 256, 0, s>>>(prof_snk, nprof, w.g);
+    prof_to_df_kernel<<<nblk((long long)nb * nv), 256, 0, s>>>(prof_src, (long long)nb * nv, g_src);
   }
   DISTIL_LAUNCH_CHECK();
   Cx<double>* Cd = reinterpret_cast<Cx<double>*>(C);
@@ -623,20 +625,20 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
       const double2* phs = (const double2*)phi_snk + ((long long)t * np + q) * T3;
       const double2* ph0 = (const double2*)phi_src + (long long)q * T3;
       const float2* ta = (const float2*)tau + (long long)t * n4 * n4;
-      Cx<double>* Cq = Cd + (long long)q * nb * nb * nt + t;
-      const long long ca = (long long)nb * nt, cb = nt;
+      Cx<double>* Cq = Cd + (long long)q * nb * nb * c_nt + c_t0 + t;
+      const long long ca = (long long)nb * c_nt, cb = c_nt;
       const int* et = w.etau + t;
       const int* es = w.esnk + (long long)t * np + q;
       const int* e0 = w.esrc + q;
       int st;
       if (mode == DISTIL_MIXED_FP16X6)
-        st = run_tp_mixed<false, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<false, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb, s);
       else if (mode == DISTIL_MIXED_BF16X6)
-        st = run_tp_mixed<true, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<true, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb, s);
       else if (mode == DISTIL_MIXED_BF16X3)
-        st = run_tp_mixed<true, true, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb, s);
+        st = run_tp_mixed<true, true, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb, s);
       else
-        st = run_tp_mixed<false, false, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, w.g, et, es, e0, nv, nb, w, Cq, ca, cb,
+        st = run_tp_mixed<false, false, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb,
                                               s);
       if (st != DISTIL_OK) return st;
     }

@@ -86,6 +86,6 @@ extern "C" int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, co
   void* scratch = nullptr;
   DISTIL_TRY(noalloc_scratch(ctx->device, reinterpret_cast<cudaStream_t>(stream), &scratch));
   // no context: no launch bookkeeping, nothing allocated on the host either
-  return correlate_plain(nullptr, mode == DISTIL_FP64, phi_snk, phi_src, tau, nt, nv, np, prof, nb, prof_per_t, C,
-                         scratch, NOALLOC_SCRATCH_BYTES, reinterpret_cast<cudaStream_t>(stream));
+  return correlate_plain(nullptr, mode == DISTIL_FP64, phi_snk, phi_src, tau, nt, nv, np, prof, prof, prof_per_t, nb,
+                         C, nt, 0, scratch, NOALLOC_SCRATCH_BYTES, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -32,7 +32,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOT
 # Every symbol include/distil.h declares.
 EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_elementals_workspace", "distil_elementals",
-           "distil_correlate_workspace", "distil_correlate", "distil_gevp",
+           "distil_correlate_workspace", "distil_correlate", "distil_correlate_slice", "distil_gevp",
+           "distil_gevp_range", "distil_optimal",
            "distil_cgemm_workspace", "distil_cgemm", "distil_correlate_noalloc",
            "distil_mode_supported", "distil_profile_enable", "distil_profile_read",
            "distil_device_status", "distil_set_tuning", "distil_get_tuning",
@@ -103,6 +104,15 @@ def _declare(L):
     L.distil_correlate.restype = c_int
     L.distil_gevp.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
     L.distil_gevp.restype = c_int
+    L.distil_gevp_range.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p,
+                                    c_void_p, c_void_p]
+    L.distil_gevp_range.restype = c_int
+    L.distil_correlate_slice.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p,
+                                         c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_size_t, c_void_p]
+    L.distil_correlate_slice.restype = c_int
+    L.distil_optimal.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p,
+                                 c_void_p]
+    L.distil_optimal.restype = c_int
     L.distil_cgemm_workspace.argtypes = [c_int, c_int, c_int, c_int, c_int, P(c_size_t)]
     L.distil_cgemm_workspace.restype = c_int
     L.distil_cgemm.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int,
@@ -236,6 +246,28 @@ def correlate(phi_snk, phi_src, tau, prof, mode="fp64", prof_per_t: bool = False
     return out
 
 
+def correlate_slice(phi_snk_t, phi_src, tau_t, prof_snk, prof_src, C, t: int, mode="fp64", workspace=None,
+                    stream=None):
+    """Column t of C[np][nb][nb][nt] from one sink timeslice: phi_snk_t [np][T3],
+    phi_src [np][T3], tau_t [4nv][4nv], prof_snk / prof_src [nb][nv] (f64)."""
+    mode = _mode(mode)
+    np_ = int(phi_snk_t.shape[0])
+    nv = int(tau_t.shape[-1]) // 4
+    nb = int(prof_snk.shape[-2])
+    nt = int(C.shape[-1])
+    for x in (phi_snk_t, phi_src, tau_t, prof_snk, prof_src, C):
+        assert x.is_cuda and x.is_contiguous()
+    ws_bytes = correlate_workspace(1, nv, np_, nb, mode)
+    if workspace is None:
+        workspace = _workspace(ws_bytes, tau_t.device)
+    ctx = context(tau_t.device.index or 0)
+    _check(lib().distil_correlate_slice(ctx, _ptr(phi_snk_t), _ptr(phi_src), _ptr(tau_t), nv, np_, _ptr(prof_snk),
+                                        _ptr(prof_src), nb, mode, _ptr(C), nt, int(t),
+                                        _ptr(workspace) if workspace is not None else None, _nbytes(workspace),
+                                        _stream(stream)))
+    return C
+
+
 def cgemm(A, B, mode="fp16x3", out=None, workspace=None, stream=None):
     """C[b] = A[b] @ B[b]^T (complex64, tensor cores, split pieces)."""
     import torch
@@ -265,6 +297,38 @@ def gevp(C, t0: int, out=None, stream=None):
     ctx = context(C.device.index or 0)
     _check(lib().distil_gevp(ctx, _ptr(C), np_, nb, nt, t0, _ptr(out), _stream(stream)))
     return out
+
+
+def gevp_range(C, t0: int, t_begin: int = 0, t_count: Optional[int] = None, lam=None, vecs=None,
+               want_vectors: bool = False, stream=None):
+    """Eigenvalues lam[np][nt][nb] (and eigenvectors vecs[np][nt][nb][nb] when
+    want_vectors or vecs is given) for timeslices [t_begin, t_begin + t_count)."""
+    import torch
+    np_, nb, _, nt = (int(s) for s in C.shape)
+    t_count = nt - t_begin if t_count is None else int(t_count)
+    assert C.dtype == torch.complex128 and C.is_cuda and C.is_contiguous()
+    if lam is None:
+        lam = torch.full((np_, nt, nb), complex("nan"), dtype=torch.complex128, device=C.device)
+    if vecs is None and want_vectors:
+        vecs = torch.full((np_, nt, nb, nb), complex("nan"), dtype=torch.complex128, device=C.device)
+    ctx = context(C.device.index or 0)
+    _check(lib().distil_gevp_range(ctx, _ptr(C), np_, nb, nt, int(t0), int(t_begin), t_count, _ptr(lam),
+                                   _ptr(vecs) if vecs is not None else None, _stream(stream)))
+    return (lam, vecs) if vecs is not None else lam
+
+
+def optimal(C, vecs, td: int, stream=None):
+    """Optimal-operator correlators copt[np][nb][nt] = u^H C(t) u for the GEVP
+    eigenvectors vecs[np][nt][nb][nb] at timeslice td, and their effective
+    masses meff[np][nb][nt] (NaN at the last timeslice)."""
+    import torch
+    np_, nb, _, nt = (int(s) for s in C.shape)
+    assert C.is_contiguous() and vecs.is_contiguous() and vecs.shape == (np_, nt, nb, nb)
+    copt = torch.empty((np_, nb, nt), dtype=torch.complex128, device=C.device)
+    meff = torch.empty((np_, nb, nt), dtype=torch.float64, device=C.device)
+    _check(lib().distil_optimal(context(C.device.index or 0), _ptr(C), np_, nb, nt, _ptr(vecs), int(td), _ptr(copt),
+                                _ptr(meff), _stream(stream)))
+    return copt, meff
 
 
 def mode_available(mode) -> bool:

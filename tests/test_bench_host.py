@@ -39,3 +39,36 @@ def test_algorithmic_flops_convention():
     assert f["elementals"] == pytest.approx(8.0 * 3 * p.V3 * p.T3 * tp)
     assert f["correlator"] == pytest.approx(8.0 * 92 * p.nb * p.nv ** 4 * tp)
     assert f["total"] == pytest.approx(f["elementals"] + f["correlator"])
+
+
+def test_shard_timeslices_cover_each_timeslice_once():
+    """Timeslice t goes to rank t mod N; a rank's share repeats when it runs
+    more steps than it has timeslices."""
+    import bench
+    nt, world = 96, 8
+    shares = [bench.shard_timeslices(nt, r, world, 12) for r in range(world)]
+    flat = sorted(t for s in shares for t in s)
+    assert flat == list(range(nt))
+    assert bench.shard_timeslices(nt, 3, 8, 14) == [3, 11, 19, 27, 35, 43, 51, 59, 67, 75, 83, 91, 3, 11]
+    assert bench.shard_timeslices(96, 0, 1, 25) == list(range(25))
+    assert bench.shard_timeslices(2, 5, 8, 3) == [1, 1, 1]          # more ranks than timeslices
+
+
+def test_elementals_issued_tiles_count_the_triangle_skip():
+    """The issued elementals MACs: every 128 x 128 tile whose smallest i is
+    below its largest j, over K padded per 4096-wide chunk.  A tiny case by
+    hand: N_v = 20, one momentum -> 190 pairs (2 row tiles), 20 (i, p) rows
+    (one 32-wide column tile, i_min = 0 < j_max): 2 tiles."""
+    import bench
+    from paper_2609_37723_b300 import synth
+    p = synth.small(4, 1, 20, mom=[(0, 0, 0)])
+    K = 3 * 64
+    assert bench.elementals_issued_cmacs(p) == 2 * 128 * 32 * 192
+    # the full-size workload issues fewer MACs than the dense tile grid and
+    # more than the useful i<j<k products
+    q = synth.config(5, 0)
+    issued = bench.elementals_issued_cmacs(q)
+    P2, R = q.nv * (q.nv - 1) // 2, q.nv * q.np_
+    dense = -(-P2 // 128) * 128 * -(-R // 128) * 128 * 3 * q.V3
+    assert 3 * q.V3 * q.T3 * q.np_ < issued < dense
+    assert K == 192

@@ -1,17 +1,26 @@
 """Tensor-core (split 16-bit, tcgen05) paths against FP64 references.
 
-Error measure for C: per entry, relative to the largest |C_ab| of its
-matrix C(p, t) (a single entry of a random complex matrix can sit
-arbitrarily close to zero; the strict per-entry relative error is printed).
+Error measures for C (tests/parity.py): the strict per-entry relative error
+|dC_ab| / |C_ab| (an entry below 1e-10 of its matrix's largest is measured
+against that largest instead), and the error relative to the largest |C_ab|
+of its matrix C(p, t) ("scaled").
 
-Tolerances.  FP16x6 represents every row to 2^-31 of its largest entry
-with fixed-point slices (9 + 11 + 11 bits) whose leading products sum
-exactly in FP32, drops terms of relative size ~1e-8, and keeps FP64 between
-the contractions: 1e-6 with a wide margin (its split GEMM is checked at
-1e-7, the rounding of its complex64 output).  BF16x6 (8 + 8 + 8 bits, 2^-24): 3e-5.  BF16x3 keeps 16 bits:
-1e-3.  FP16x3 keeps 22 bits in floating pieces, but the tensor core's FP32
-accumulation is not correctly rounded: its error grows with the number of
-accumulated MMAs (measured about 2.5e-8 per step): 1e-4."""
+FP16X6 is the mode that must match the FP64 oracle to 1e-6 per entry: it
+represents every row to 2^-31 of its largest entry with fixed-point slices
+(9 + 11 + 11 bits) whose leading products sum exactly in FP32, drops terms
+of relative size ~1e-8 and keeps double-float arithmetic between the
+contractions; its gate is the strict per-entry 1e-6.
+
+The other modes are gated at matrix scale by bounds from their
+arithmetic.  BF16X6 (8 + 8 + 8 bits): each operand row holds 2^-(H+2W) =
+2^-23 of its largest entry (H = 7); a contraction of two such operands
+carries ~2 x 2^-23 x (row maximum / row rms, ~3 for Gaussian rows) ~ 7e-7,
+and C passes through four (step i, step j, source, dot): ~3e-6 -> 1e-5.
+BF16X3 (8 + 8 bits, 2^-15 per row): ~1.5e-4 per contraction -> 1e-3.
+FP16X3 (floating h + l, 22 bits) is limited by the tensor core's FP32
+accumulation, which is not correctly rounded (measured ~2.5e-8 per
+accumulated MMA): 1e-4.  The strict per-entry errors are printed.
+"""
 import numpy as np
 import pytest
 
@@ -22,7 +31,12 @@ from parity import max_c_error, max_c_scaled_error, normwise
 pytestmark = pytest.mark.gpu
 
 MODES = ["fp16x6", "bf16x6", "bf16x3", "fp16x3"]
-TOL_C = {"fp16x6": 1e-6, "fp16x3": 1e-4, "bf16x6": 3e-5, "bf16x3": 1e-3}
+TOL_C = {"fp16x6": 1e-6, "fp16x3": 1e-4, "bf16x6": 1e-5, "bf16x3": 1e-3}
+
+
+def gate(mode, got, ref):
+    """The strict per-entry error for FP16X6, the matrix-scale error otherwise."""
+    return max_c_error(got, ref) if mode == "fp16x6" else max_c_scaled_error(got, ref)
 
 
 def T(x):
@@ -60,9 +74,9 @@ def test_correlate_mixed_c1(cuda_lib, mode):
     phi = orc.elementals(v, p.L, p.mom)          # complex128, as the mixed path keeps them
     ref = orc.correlator(phi, phi[0], tau, p.prof)
     got = distil.correlate(T(phi), T(phi[0]), T(tau), T(p.prof), mode).cpu().numpy()
-    e = max_c_scaled_error(got, ref)
-    print(f"correlate {mode} c1: scaled {e:.2e} strict per-entry {max_c_error(got, ref):.2e}")
-    assert e < TOL_C[mode]
+    print(f"correlate {mode} c1: scaled {max_c_scaled_error(got, ref):.2e} strict per-entry "
+          f"{max_c_error(got, ref):.2e}")
+    assert gate(mode, got, ref) < TOL_C[mode]
 
 
 @pytest.mark.parametrize("mode", ["fp16x6", "bf16x6"])
@@ -76,9 +90,9 @@ def test_correlate_mixed_odd(cuda_lib, mode, L, nt, nv, nb):
     phi = orc.elementals(v, p.L, p.mom)
     ref = orc.correlator(phi, phi[0], tau, p.prof)
     got = distil.correlate(T(phi), T(phi[0]), T(tau), T(p.prof), mode).cpu().numpy()
-    e = max_c_scaled_error(got, ref)
-    print(f"correlate {mode} L={L} nv={nv}: scaled {e:.2e} strict {max_c_error(got, ref):.2e}")
-    assert e < TOL_C[mode]
+    print(f"correlate {mode} L={L} nv={nv}: scaled {max_c_scaled_error(got, ref):.2e} strict "
+          f"{max_c_error(got, ref):.2e}")
+    assert gate(mode, got, ref) < TOL_C[mode]
 
 
 # ------------------------------------------------------------------ elementals
@@ -116,8 +130,8 @@ def test_chain_fp16x6_c1(cuda_lib):
     ref_C = orc.correlator(ref_phi, ref_phi[0], tau, p.prof)
     ph = distil.elementals(T(v), p.L, p.mom, "fp16x6")
     C = distil.correlate(ph, ph[0].contiguous(), T(tau), T(p.prof), "fp16x6")
-    e = max_c_scaled_error(C.cpu().numpy(), ref_C)
-    print(f"chain fp16x6 c1: scaled {e:.2e} strict {max_c_error(C.cpu().numpy(), ref_C):.2e}")
+    e = max_c_error(C.cpu().numpy(), ref_C)
+    print(f"chain fp16x6 c1: scaled {max_c_scaled_error(C.cpu().numpy(), ref_C):.2e} strict {e:.2e}")
     assert e < 1e-6
 
 
@@ -137,5 +151,5 @@ def test_misaligned_workspace_rejected(cuda_lib):
     with pytest.raises(distil.DistilError, match="misaligned"):
         distil.correlate(T(phi), T(phi[0]), T(tau), T(p.prof), "fp16x6", workspace=ws[16:])
     got = distil.correlate(T(phi), T(phi[0]), T(tau), T(p.prof), "fp16x6", workspace=ws[256:]).cpu().numpy()
-    assert max_c_scaled_error(got, orc.correlator(phi, phi[0], tau, p.prof)) < TOL_C["fp16x6"]
+    assert max_c_error(got, orc.correlator(phi, phi[0], tau, p.prof)) < TOL_C["fp16x6"]
     assert distil.device_status() == 0

@@ -6,7 +6,7 @@ import pytest
 
 from paper_2609_37723_b300 import synth
 from oracle import nucleon as orc
-from parity import max_c_scaled_error
+from parity import max_c_error, max_c_scaled_error
 
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +54,9 @@ def test_plan_uneven_ensemble_mixed(cuda_lib, autotune):
     for (p, v, tau), c, got in zip(ens, cfgs, first):
         phi = orc.elementals(v.astype(np.complex128), p.L, p.mom)
         ref = orc.correlator(phi, phi[0], tau.astype(np.complex128), p.prof)
-        assert max_c_scaled_error(got, ref) < 2e-6, p.nv
+        print(f"plan fp16x6 N_v={p.nv}: strict per-entry {max_c_error(got, ref):.2e} "
+              f"(scaled {max_c_scaled_error(got, ref):.2e})")
+        assert max_c_error(got, ref) < 1e-6, p.nv
         # the same pipeline called eagerly with the plan's kernel variants
         phi_d = distil.elementals(c["v"], p.L, p.mom, "fp16x6")
         eager = distil.correlate(phi_d, phi_d[0], c["tau"], c["prof"], "fp16x6").cpu().numpy()

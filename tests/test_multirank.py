@@ -66,3 +66,46 @@ def test_single_rank_needs_no_process_group():
     import torch
     local = {c: torch.full((1,), float(c)) for c in (2, 0, 1)}
     assert [float(t[0]) for t in bench.gather_C(local, 3)] == [0.0, 1.0, 2.0]
+
+
+def _rank_timeslices(rank, world, port, outdir):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        nt = 10
+        mine = bench.shard_timeslices(nt, rank, world, 7)        # 5 distinct timeslices, two repeated
+        C = np.zeros((2, 3, 3, nt), dtype=np.complex128)
+        for t in mine:                                          # this rank fills only its columns
+            C[..., t] = complex(t, rank)
+        got = bench.gather_columns(C, [0] + mine, dist)         # every rank also computed t = 0 itself
+        value, all_entries, ms_max = bench.job_throughput(2 * 9.0, 100.0 + 10 * rank, 7, dist)
+        res = {"mine": mine, "all": all_entries, "ms": ms_max,
+               "cols": None if got is None else {str(t): [c.real.flat[0], c.imag.flat[0]] for t, c in got.items()}}
+        with open(os.path.join(outdir, f"ts{rank}.json"), "w") as f:
+            json.dump(res, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_one_configuration_by_timeslice(tmp_path):
+    """One configuration split over ranks by timeslice: rank r takes t = r
+    mod N, the columns of C reach rank 0 after the run (each from the rank
+    that computed it), and the job throughput sums the ranks' entries over
+    the slowest rank's time."""
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_rank_timeslices, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    res = [json.load(open(tmp_path / f"ts{r}.json")) for r in range(world)]
+    assert res[0]["mine"] == [0, 2, 4, 6, 8, 0, 2] and res[1]["mine"] == [1, 3, 5, 7, 9, 1, 3]
+    cols = res[0]["cols"]
+    assert sorted(int(t) for t in cols) == list(range(10))
+    for t, (re, im) in cols.items():
+        t = int(t)
+        if t == 0:
+            continue                      # every rank has a t = 0 column; the last gathered wins
+        assert re == t and im == t % 2
+    assert res[1]["cols"] is None
+    assert res[0]["all"] == res[1]["all"] == 36.0 and res[0]["ms"] == 110.0
