@@ -7,20 +7,27 @@
 // Split schemes.  A row of an operand with max |x| < 2^e is represented as
 //  * fixed-point slices: t = x 2^(H-e) = hi + 2^-W mid + 2^-2W lo with hi,
 //    mid, lo integers (|hi| <= 2^H, |mid|, |lo| <= 2^(W-1)), exact in the
-//    16-bit type (FP16: W = 11, H <= 10; BF16: W = 8, H <= 7).  The products
-//    hi*hi are integers, so the sums of the leading slices are integers that
-//    the tensor core accumulates exactly in FP32, whatever its rounding, as
-//    long as the partial sums stay below 2^24 (guaranteed for
-//    K <= 2^(23 - 2H); for rows of random sign the partial sums grow like
-//    sqrt(K) |hi|^2 and stay far below that for the K used here).  The cross
-//    terms go to a second accumulator weighted 2^-W; it holds values of about
-//    2^-W |mid/hi| of the result, so its inexact rounding stays far below the
-//    target.  A pieces: hi, mid, lo 2^-W.  B pieces: hi, mid, mid 2^-W,
-//    lo 2^-W (hi*lo, mid*mid, lo*hi all carry 2^-2W).  Dropped terms
-//    (mid*lo, lo*mid, lo*lo) are of relative size 2^-3W |mid lo| / |hi|^2,
-//    so H trades the dropped-term error against the exactness range: H = 9
-//    for the short (K <= 4 N_v) mode contractions, H = 10 with K chunks of
-//    4096 for the long (K = 3 V3) elemental contraction.
+//    16-bit type (FP16: W = 11, H <= 11; BF16: W = 8, H <= 7).  Products of
+//    integer slices are integers, which the tensor core's FP32 accumulation
+//    adds exactly, whatever its rounding, while the partial sums stay below
+//    2^24; each weight class gets its own TMEM accumulator pair:
+//      class 0  hi*hi                     (exact)
+//      class 1  hi*mid + mid*hi           (exact while below 2^24)
+//      class 2  hi*lo, mid*mid, lo*hi [, lo*mid, mid*lo]   (pre-scaled by
+//               2^-W, so fractional: inexact, but ~2^-11 of class 1)
+//    With two pairs classes 1 and 2 share one accumulator, whose rounding
+//    then drifts with the number of accumulated MMAs (measured ~2.5e-8 of
+//    the accumulator per MMA): fine for K <= N_v, not for longer K.  The
+//    terms dropped by the 6-product scheme (mid*lo, lo*mid, lo*lo) are of
+//    relative size 2^-(W+2+2H) per product, independent of how many bits lo
+//    keeps; the 8-product scheme keeps mid*lo and lo*mid (dropping
+//    2^-(2W+2+2H)).  Choices, from an emulation of the split on full-size
+//    rows and the measured parity:
+//      mode contractions (K <= 4 N_v)  H = 10, 6 products, three pairs for
+//                                      K = 4 N_v, two for K = N_v
+//      elementals (4096-long K chunks) H = 8, 8 products, three pairs
+//    A pieces: hi, mid, lo 2^-W (3) or hi, mid, mid 2^-W, lo 2^-W (4).
+//    B pieces: hi, mid, mid 2^-W, lo 2^-W.
 //  * floating pieces (FP16X3): t = x 2^(14-e) = h + l, h = fp16(t),
 //    l = fp16(t - h); accumulation rounding is not exact.
 #pragma once
@@ -39,21 +46,33 @@ struct Scheme {
   int H, W;    // fixed point: t = x 2^(H - e), slices of W bits; floating: H = 14
   int na, nb;  // pieces of the A / B operand
   int nprod;
-  int pa[6], pb[6], acc[6];
+  int pa[8], pb[8], acc[8];
   float w1;    // weight of the second accumulator (2^-W)
   int shift;   // D *= 2^(eA + eB - shift), shift = 2H
 };
 
 inline Scheme scheme_of(int mode) {
   if (mode == DISTIL_MIXED_FP16X6)
-    return Scheme{false, true, 9, 11, 3, 4, 6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 3, 2, 0}, {0, 1, 1, 1, 1, 1},
-                  1.f / 2048.f, 18};
+    return Scheme{false, true, 10, 11, 3, 4, 6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 3, 2, 0}, {0, 1, 1, 1, 1, 1},
+                  1.f / 2048.f, 20};
   if (mode == DISTIL_MIXED_BF16X6)
     return Scheme{true, true, 7, 8, 3, 4, 6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 3, 2, 0}, {0, 1, 1, 1, 1, 1},
                   1.f / 256.f, 14};
   if (mode == DISTIL_MIXED_BF16X3)
     return Scheme{true, true, 7, 8, 2, 2, 3, {0, 0, 1}, {0, 1, 0}, {0, 1, 1}, 1.f / 256.f, 14};
   return Scheme{false, false, 14, 0, 2, 2, 3, {0, 0, 1}, {0, 1, 0}, {0, 1, 1}, 1.f, 28};  // FP16X3
+}
+
+// The FP16X6 elementals (K = 3 V3 in 4096-long chunks) use 4 x 4 pieces
+// and eight products (the third-order lo*mid and mid*lo kept) with an
+// 8-bit leading slice: the hi*mid + mid*hi sums of a chunk stay below 2^24
+// and add exactly in their own accumulator, and the dropped terms (lo*lo,
+// 2^-(2W+2+2H)) are far below the target.  Other modes use their scheme.
+inline Scheme elementals_scheme_of(int mode) {
+  if (mode == DISTIL_MIXED_FP16X6)
+    return Scheme{false, true, 8, 11, 4, 4, 8, {0, 0, 1, 0, 3, 1, 3, 2}, {0, 1, 0, 3, 0, 2, 2, 3},
+                  {0, 1, 1, 2, 2, 2, 2, 2}, 1.f / 2048.f, 16};
+  return scheme_of(mode);
 }
 
 inline void fill_products(tc::GemmCfg& cfg, const Scheme& s) {

@@ -474,36 +474,43 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
 }
 
 // Mode-contraction GEMM in the kernel variant the context's tuning table
-// names for this site: 0 = one 128 x 128 tile per CTA (wide MMAs, no
-// overlap of epilogue and MMAs), 1 = persistent CTAs with two 128 x 64
-// accumulator sets (the epilogue of one tile overlaps the MMAs of the
-// next), 2 = the same with the whole-K A tile resident in shared memory
-// across the column tiles of a batch (K <= 128; else variant 1).  All
-// accumulate every element over K in the same order, so they give
-// identical results.
+// names for this site: 0 = one 128 x NT tile per CTA (wide MMAs, no overlap
+// of epilogue and MMAs), 1 = persistent CTAs with two accumulator sets (the
+// epilogue of one tile overlaps the MMAs of the next), 2 = the same with the
+// whole-K A tile resident in shared memory across the column tiles of a
+// batch (K <= 128; else variant 1).  NACC is a property of the site, not of
+// the variant: step j (K = 4 N_v) accumulates the 6-product schemes in three
+// pairs (exact cross terms; the second-order terms drift with K otherwise),
+// the short contractions (K = N_v) in two.  All variants of a site
+// accumulate every element over K in the same order into the same pairs, so
+// they give identical results.
 enum GemmSite { SITE_STEP_I = 0, SITE_STEP_J = 1, SITE_SOURCE = 2 };
-template <bool BF16, int NPLA, int NPLB, class Epi>
+template <bool BF16, int NPLA, int NPLB, int NACC, class Epi>
 static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& A, const Planes& B,
                 const tc::GemmCfg& cfg, int batch, const Epi& epi, cudaStream_t s) {
   constexpr int KC = 16;
   constexpr int NKA = 8;  // resident A covers K <= 128
-  if (ctx->tune[site] == 2 && cfg.K <= NKA * KC && cfg.N > 32)
-    return tc::launch_gemm_ares<64, KC, NPLA, NPLB, NKA, BF16>(ctx, name, A, B, cfg, batch, epi, s);
+  constexpr int NTP = NACC == 3 ? 32 : 64;    // persistent: two sets of 2 NACC NT columns
+  constexpr int NTW = NACC == 3 ? 80 : 128;   // one-tile: 2 NACC NT columns
+  if constexpr (NACC == 2) {
+    if (ctx->tune[site] == 2 && cfg.K <= NKA * KC && cfg.N > 32)
+      return tc::launch_gemm_ares<64, KC, NPLA, NPLB, NKA, BF16, NACC>(ctx, name, A, B, cfg, batch, epi, s);
+  }
   if (ctx->tune[site] >= 1) {
     if (cfg.N > 32)
-      return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(
+      return tc::launch_gemm_persistent<NTP, KC, NPLA, NPLB, tc::max_stages<NTP, KC, NPLA, NPLB>(), BF16, NACC>(
           ctx, name, A, B, cfg, batch, epi, s);
-    return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16>(
+    return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16, NACC>(
         ctx, name, A, B, cfg, batch, epi, s);
   }
   if (cfg.N > 64)
-    return tc::launch_gemm<128, KC, NPLA, NPLB, tc::max_stages<128, KC, NPLA, NPLB>(), BF16>(ctx, name, A, B, cfg,
-                                                                                            batch, epi, s);
+    return tc::launch_gemm<NTW, KC, NPLA, NPLB, tc::max_stages<NTW, KC, NPLA, NPLB>(), BF16, NACC>(
+        ctx, name, A, B, cfg, batch, epi, s);
   if (cfg.N > 32)
-    return tc::launch_gemm<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16>(ctx, name, A, B, cfg,
-                                                                                          batch, epi, s);
-  return tc::launch_gemm<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16>(ctx, name, A, B, cfg,
-                                                                                        batch, epi, s);
+    return tc::launch_gemm<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16, NACC>(ctx, name, A, B, cfg,
+                                                                                                batch, epi, s);
+  return tc::launch_gemm<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16, NACC>(ctx, name, A, B, cfg,
+                                                                                              batch, epi, s);
 }
 
 static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
@@ -547,7 +554,7 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
     cfg.b = tc::OpMap{12, nb, 1, 0, 0, (int)n2, w.eG};
     EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
   }
   // ---- source: batch (b, c) = nb x 5; X[b][c][pair][k]
   {
@@ -560,7 +567,7 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.out = w.X;
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
     epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, SITE_SOURCE, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_SOURCE, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
   }
   // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
@@ -574,7 +581,7 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
   }
   // ---- dot
   {

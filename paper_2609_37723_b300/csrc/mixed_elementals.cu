@@ -4,7 +4,8 @@
 //   E_(i,q)(x,a) = exp(-i p_q.x) v_i^a(x),   W_(j,k) = v_j x v_k (colour cross product)
 //
 // per timeslice as one complex GEMM with M = pairs j<k (ordered by j, then
-// k), N = (i, q) rows and K = (site, colour).  K is cut into chunks of
+// k), N = (i, q) rows and K = (site, colour) (FP16X6: 4 x 4 fixed-point
+// pieces, eight products, elementals_scheme_of).  K is cut into chunks of
 // EL_KC values: per chunk the operands are formed from the eigenvectors in
 // double-float arithmetic (the cross products exactly, by TwoProduct) and
 // split into 16-bit pieces with per-(row, chunk) exponents; the tensor
@@ -24,7 +25,6 @@ namespace distil {
 using tc::Planes;
 
 constexpr int EL_KC = 4096;  // K values per accumulation chunk
-constexpr int EL_H = 10;     // leading-slice width of the FP16 elemental operands
 
 // pairs in j-major order: q -> (j, k), first index j, then k = j+1..n-1
 __host__ __device__ __forceinline__ long long jmajor_first(long long j, long long n) { return j * (2 * n - j - 1) / 2; }
@@ -180,7 +180,7 @@ static ElemWs carve_elem(Arena& ar, const Scheme& sc, int L, int nv, int np) {
 size_t elementals_mixed_workspace(int L, int nt, int nv, int np, int mode) {
   (void)nt;
   Arena ar;
-  carve_elem(ar, scheme_of(mode), L, nv, np);
+  carve_elem(ar, elementals_scheme_of(mode), L, nv, np);
   return ar.used + 256;
 }
 
@@ -204,17 +204,22 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
     cfg.b = tc::OpMap{1, 1, 0, 0, 0, (int)R, w.eE};
     EpiPhiAcc epi{{}, w.acc, w.pairs, P2, (int)R, mom.np, K0 == 0 ? 1 : 0, 128};
     // K = 4096 per chunk: a deep ring of 16-wide K steps keeps enough of the
-    // operand stream (the A pieces come from HBM) in flight
-    constexpr int ST = tc::max_stages<128, 16, NPLA, NPLB>();
+    // operand stream (the A pieces come from HBM) in flight.  The 6-product
+    // schemes accumulate in three pairs (exact cross terms), which leaves
+    // TMEM room for 80-wide N tiles.
+    constexpr int NACC = NPLA >= 6 ? 3 : 2;
+    constexpr int NTW = NACC == 3 ? 80 : 128;
+    constexpr int ST = tc::max_stages<NTW, 16, NPLA, NPLB>();
     int st;
     if (R > 64) {
-      st = tc::launch_gemm<128, 16, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+      epi.nt = NTW;
+      st = tc::launch_gemm<NTW, 16, NPLA, NPLB, ST, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     } else if (R > 32) {
       epi.nt = 64;
-      st = tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+      st = tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     } else {
       epi.nt = 32;
-      st = tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+      st = tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     }
     DISTIL_TRY(st);
   }
@@ -230,7 +235,7 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
 int elementals_mixed(distil_ctx* ctx, const Cx<float>* v, int L, int nt, int nv, const int32_t* mom, int np,
                      int mode, void* phi, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (comb3(nv) == 0) return DISTIL_OK;
-  const Scheme sch = scheme_of(mode);
+  const Scheme sch = elementals_scheme_of(mode);
   Arena ar(ws, ws_bytes);
   ElemWs w = carve_elem(ar, sch, L, nv, np);
   if (!ar.fits()) {
@@ -249,14 +254,13 @@ int elementals_mixed(distil_ctx* ctx, const Cx<float>* v, int L, int nt, int nv,
   }
   DISTIL_LAUNCH_CHECK();
   const long long V3 = (long long)L * L * L, T3 = comb3(nv);
-  // the fixed-point FP16 elementals use their own leading-slice width (long K)
-  const int H = (sch.fixed && !sch.bf16) ? EL_H : sch.H;
+  const int H = sch.H;
   for (int t = 0; t < nt; ++t) {
     const float2* vt = reinterpret_cast<const float2*>(v) + (long long)t * nv * V3 * 3;
     double2* pt = reinterpret_cast<double2*>(phi) + (long long)t * np * T3;
     int st;
     if (mode == DISTIL_MIXED_FP16X6)
-      st = elem_t<false, true, 3, 4>(ctx, sch, H, vt, L, nv, m, pt, w, s);
+      st = elem_t<false, true, 4, 4>(ctx, sch, H, vt, L, nv, m, pt, w, s);
     else if (mode == DISTIL_MIXED_BF16X6)
       st = elem_t<true, true, 3, 4>(ctx, sch, H, vt, L, nv, m, pt, w, s);
     else if (mode == DISTIL_MIXED_BF16X3)

@@ -42,10 +42,14 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
     set_error("distil_cgemm: workspace too small");
     return DISTIL_ENOMEM;
   }
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_cgemm", BatchRows{A, K}, (long long)batch * M, M, K, sch.H, PA, ld, eA, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_cgemm", BatchRows{B, K}, (long long)batch * N, N, K, sch.H, PB, ld, eB, s)));
+  // fixed-point FP16: a narrower leading slice for long K keeps the exact
+  // hi*hi sums below 2^24 (they grow like 2^2H sqrt(K) for rows of random sign)
+  const int H = (FIXED && !BF16) ? (K <= 1024 ? sch.H : K <= 4096 ? 9 : K <= 16384 ? 8 : 7) : sch.H;
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_cgemm", BatchRows{A, K}, (long long)batch * M, M, K, H, PA, ld, eA, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_cgemm", BatchRows{B, K}, (long long)batch * N, N, K, H, PB, ld, eB, s)));
   tc::GemmCfg cfg{};
   fill_products(cfg, sch);
+  cfg.shift = 2 * H;
   cfg.M = M; cfg.N = N; cfg.K = K;
   cfg.a = tc::OpMap{1, batch, 1, 0, 0, M, eA};
   cfg.b = tc::OpMap{1, batch, 1, 0, 0, N, eB};
@@ -53,10 +57,14 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
   tc::Planes pa = planes_of(PA, K, M, batch, NPLA, ld);
   tc::Planes pb = planes_of(PB, K, N, batch, NPLB, ld);
   EpiStoreC64 epi{{}, C, (long long)M * N, N, N};
+  // the 6-product schemes accumulate in three pairs (exact cross terms)
+  constexpr int NACC = NPLA == 6 ? 3 : 2;
+  constexpr int NTW = NACC == 3 ? 80 : 128;
   constexpr int ST = (NPLA + NPLB) > 8 ? 2 : 3;
-  if (N > 64) return tc::launch_gemm<128, 32, NPLA, NPLB, ST, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
-  if (N > 32) return tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
-  return tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
+  if (N > 64)
+    return tc::launch_gemm<NTW, 32, NPLA, NPLB, ST, BF16, NACC>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
+  if (N > 32) return tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
+  return tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
 }
 
 int cgemm_mixed(distil_ctx* ctx, int mode, const void* A, const void* B, void* C, int M, int N, int K, int batch,

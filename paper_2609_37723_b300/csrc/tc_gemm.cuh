@@ -9,17 +9,17 @@
 // accumulator pair `acc` in TMEM:
 //   D_re[acc] += A_re[pa] B_re[pb] + (-A_im[pa]) B_im[pb]   (negate-A descriptor)
 //   D_im[acc] += A_re[pa] B_im[pb] + A_im[pa] B_re[pb]
-// Two accumulator pairs exist so that the leading product of a fixed-point
-// split (integer-valued slices) sums exactly in its own FP32 accumulator,
-// whatever the tensor core's accumulation rounding; every scheme puts at
-// least one product into each pair.  The epilogue scales both by
-// 2^(eA[row] + eB[col] - shift) (the second also by w1, all exact powers of
-// two) and hands the pair to the functor, which keeps D = D[0] + D[1] as a
-// double-float.
+// Two or three accumulator pairs exist (SchemeProducts) so that the products
+// of integer slices of a fixed-point split sum exactly in FP32 accumulators
+// of their own, whatever the tensor core's accumulation rounding; every
+// scheme puts at least one product into each pair.  The epilogue scales
+// them by 2^(eA[row] + eB[col] - shift) (the cross-term pairs also by w1,
+// all exact powers of two) and hands the leading and the cross-term sums to
+// the functor, which keeps D = D[0] + D[1] as a double-float.
 //
 // One CTA computes a 128 x NT tile: warp 0 issues TMA loads into a STAGES-deep
 // ring, warp 1 allocates TMEM and issues the MMAs, and 8 epilogue warps (two
-// per TMEM lane quarter, each owning half of the columns) read the
+// per TMEM lane quarter, taking alternate 16-column slices) read the
 // accumulators back (tcgen05.ld) and hand 16-column slices to the epilogue
 // functor.  All waits are bounded (tc.cuh).
 #pragma once
@@ -43,27 +43,58 @@ struct GemmCfg {
   int M, N, K;
   OpMap a, b;
   int nprod;
-  int pa[6], pb[6], acc[6];
-  float w1;   // weight of the second accumulator pair
+  int pa[8], pb[8], acc[8];
+  float w1;   // weight of the cross-term accumulator pairs
   int shift;  // D *= 2^(eA + eB - shift)
   unsigned* err;
 };
 
 // Products of the split schemes, by operand planes: 3 x 4 pieces (6
 // products, fixed point) or 2 x 2 pieces (3 products).  A product (pa, pb,
-// acc) adds A[pa] B[pb] into accumulator pair acc.
-template <int NPLA, int NPLB>
+// acc) adds A[pa] B[pb] into accumulator pair acc.  The 6-product scheme
+// comes with two or three accumulator pairs (NACC):
+//   NACC = 2: hi*hi | every cross term
+//   NACC = 3: hi*hi | hi*mid + mid*hi | the second-order terms
+// With three pairs the first two hold sums of products of integer slices
+// only, which the FP32 accumulation adds exactly while the partial sums stay
+// below 2^24; the third holds the pre-scaled second-order terms, about 2^-11
+// of the second, whose inexact accumulation no longer drifts with K at the
+// level of the result.  The 3-product schemes have two pairs.
+template <int NPLA, int NPLB, int NACC>
 struct SchemeProducts;
 template <>
-struct SchemeProducts<6, 8> {
+struct SchemeProducts<6, 8, 2> {
   static constexpr int n = 6;
   static constexpr int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 3, 2, 0}, acc[6] = {0, 1, 1, 1, 1, 1};
 };
 template <>
-struct SchemeProducts<4, 4> {
+struct SchemeProducts<6, 8, 3> {
+  static constexpr int n = 6;
+  static constexpr int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 3, 2, 0}, acc[6] = {0, 1, 1, 2, 2, 2};
+};
+// 4 x 4 pieces (hi, mid, mid 2^-W, lo 2^-W on both sides), 8 products: the
+// six of the 3 x 4 scheme plus the third-order lo*mid and mid*lo, which the
+// 6-product scheme drops (a term of relative size 2^-(W+2+2H) per product
+// that does not shrink with the leading-slice width H).  Three pairs:
+// hi*hi | hi*mid + mid*hi | the second- and third-order terms.
+template <>
+struct SchemeProducts<8, 8, 3> {
+  static constexpr int n = 8;
+  static constexpr int pa[8] = {0, 0, 1, 0, 3, 1, 3, 2}, pb[8] = {0, 1, 0, 3, 0, 2, 2, 3},
+                       acc[8] = {0, 1, 1, 2, 2, 2, 2, 2};
+};
+template <>
+struct SchemeProducts<4, 4, 2> {
   static constexpr int n = 3;
   static constexpr int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0}, acc[3] = {0, 1, 1};
 };
+
+// TMEM columns an allocation of `cols` needs: a power of two >= 32.
+__host__ __device__ constexpr uint32_t tmem_alloc_cols(uint32_t cols) {
+  uint32_t a = 32;
+  while (a < cols) a <<= 1;
+  return a;
+}
 
 // One real MMA: A plane, B plane, accumulator (pair * 2 + re/im), negate B,
 // first write of its accumulator.
@@ -77,14 +108,14 @@ struct MmaOp {
 // Built at compile time, so the single issuing thread only adds constant
 // offsets to two descriptors per stage and keeps the tensor pipe fed (a
 // schedule decoded at run time left it waiting on the issuer).
-template <int NPLA, int NPLB>
+template <int NPLA, int NPLB, int NACC>
 struct MmaSchedule {
-  using P = SchemeProducts<NPLA, NPLB>;
+  using P = SchemeProducts<NPLA, NPLB, NACC>;
   static constexpr int n = 4 * P::n;
   MmaOp ops[4 * P::n];
   constexpr MmaSchedule() : ops{} {
     int k = 0;
-    bool written[4] = {false, false, false, false};
+    bool written[6] = {false, false, false, false, false, false};
     for (int pa = 0; pa < NPLA / 2; ++pa) {
       for (int part = 0; part < 2; ++part) {
         for (int p = 0; p < P::n; ++p) {
@@ -141,12 +172,54 @@ constexpr int max_stages() {
 
 constexpr int TC_THREADS = 64 + 8 * 32;  // producer, MMA issuer, 8 epilogue warps
 
-template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
+// Epilogue of one 16-column slice c of a tile for this thread's row: read
+// the NACC accumulator pairs at TMEM address tl (D0_re | D0_im | D1_re |
+// D1_im [| D2_re | D2_im], NT columns each; every lane of the warp takes
+// part), scale by the exact powers of two 2^(eA + eB - shift) (and w1 for
+// the cross terms, D1 + D2 summed in FP32) and hand the pair to the
+// epilogue functor.
+template <int NT, int NACC, class Epi>
+__device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& st, const GemmCfg& cfg, uint32_t tl,
+                                          int c, int batch, int row, int n_tile, int ea, int cb) {
+  uint32_t r0[16], i0[16], r1[16], i1[16], r2[16], i2[16];
+  tmem_ld16(tl + c * 16, r0);
+  tmem_ld16(tl + NT + c * 16, i0);
+  tmem_ld16(tl + 2 * NT + c * 16, r1);
+  tmem_ld16(tl + 3 * NT + c * 16, i1);
+  if constexpr (NACC == 3) {
+    tmem_ld16(tl + 4 * NT + c * 16, r2);
+    tmem_ld16(tl + 5 * NT + c * 16, i2);
+  }
+  tmem_wait_ld();
+  const int col0 = n_tile * NT + c * 16;
+  if (row < cfg.M) {
+    float re0[16], re1[16], im0[16], im1[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int col = col0 + e;
+      const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
+      const float f = pow2f(ea + eb - cfg.shift);  // exact power-of-two scalings
+      const float f1 = f * cfg.w1;
+      float x1 = __uint_as_float(r1[e]), y1 = __uint_as_float(i1[e]);
+      if constexpr (NACC == 3) {
+        x1 += __uint_as_float(r2[e]);
+        y1 += __uint_as_float(i2[e]);
+      }
+      re0[e] = __uint_as_float(r0[e]) * f;
+      im0[e] = __uint_as_float(i0[e]) * f;
+      re1[e] = x1 * f1;
+      im1[e] = y1 * f1;
+    }
+    epi(st, batch, row, col0, re0, re1, im0, im1);
+  }
+}
+
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC, class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    GemmCfg cfg, Epi epi) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
-  static_assert(NT % 16 == 0 && NT >= 32 && NT <= 128, "N tile");
+  static_assert(NT % 16 == 0 && NT >= 32 && NT <= 128 && 2 * NACC * NT <= 512, "N tile / TMEM columns");
   static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
   // a CTA of a launch that already hit a timeout does nothing; the epilogue
   // may declare a tile empty (no output it keeps) before anything is set up
@@ -166,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tile = blockIdx.x, m_tile = blockIdx.y, batch = blockIdx.z;
   const int nk = (cfg.K + KC - 1) / KC;
-  constexpr uint32_t TCOLS = 4 * NT;  // D0_re | D0_im | D1_re | D1_im
+  constexpr uint32_t TCOLS = tmem_alloc_cols(2 * NACC * NT);  // D0_re | D0_im | D1_re | D1_im [| D2_re | D2_im]
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -211,7 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------------------------------------------------------- MMA issuer
     constexpr uint32_t id = idesc_f16(128, NT, BF16, false);
     constexpr uint32_t idn = idesc_f16(128, NT, BF16, false, true);
-    constexpr MmaSchedule<NPLA, NPLB> S{};
+    constexpr MmaSchedule<NPLA, NPLB, NACC> S{};
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (kb / STAGES) & 1;
@@ -254,30 +327,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
       const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = half * (NT / 32); c < (half + 1) * (NT / 32); ++c) {
-        uint32_t r0[16], i0[16], r1[16], i1[16];
-        tmem_ld16(tl + c * 16, r0);
-        tmem_ld16(tl + NT + c * 16, i0);
-        tmem_ld16(tl + 2 * NT + c * 16, r1);
-        tmem_ld16(tl + 3 * NT + c * 16, i1);
-        tmem_wait_ld();
-        const int col0 = n_tile * NT + c * 16;
-        if (row < cfg.M) {
-          float re0[16], re1[16], im0[16], im1[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int col = col0 + e;
-            const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
-            const float f = pow2f(ea + eb - cfg.shift);  // exact power-of-two scalings
-            const float f1 = f * cfg.w1;
-            re0[e] = __uint_as_float(r0[e]) * f;
-            im0[e] = __uint_as_float(i0[e]) * f;
-            re1[e] = __uint_as_float(r1[e]) * f1;
-            im1[e] = __uint_as_float(i1[e]) * f1;
-          }
-          epi(st, batch, row, col0, re0, re1, im0, im1);
-        }
-      }
+      for (int c = half; c < NT / 16; c += 2) epi_slice<NT, NACC>(epi, st, cfg, tl, c, batch, row, n_tile, ea, cb);
       epi.end(st, batch);
     }
     tc_fence_before();
@@ -309,12 +359,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 //   tempty[b]            epilogue -> MMA: set b has been read (8 warp arrivals)
 // Every wait is bounded; on expiry the error word is set, every role leaves
 // its loop, copies still in flight are waited for and TMEM is freed.
-template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC, class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                               GemmCfg cfg, Epi epi, int n_tiles, int m_tiles, int total_tiles) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
-  static_assert(NT % 16 == 0 && NT >= 32 && 8 * NT <= 512, "two accumulator sets must fit TMEM");
+  static_assert(NT % 16 == 0 && NT >= 32 && 4 * NACC * NT <= 512, "two accumulator sets must fit TMEM");
   static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
   extern __shared__ uint8_t smem_raw[];
@@ -332,8 +382,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (cfg.K + KC - 1) / KC;
-  constexpr uint32_t SET = 4 * NT;  // D0_re | D0_im | D1_re | D1_im
-  constexpr uint32_t TCOLS = 2 * SET;
+  constexpr uint32_t SET = 2 * NACC * NT;  // D0_re | D0_im | D1_re | D1_im [| D2_re | D2_im]
+  constexpr uint32_t TCOLS = tmem_alloc_cols(2 * SET);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -385,7 +435,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------------------------------------------------------- MMA issuer
     constexpr uint32_t id = idesc_f16(128, NT, BF16, false);
     constexpr uint32_t idn = idesc_f16(128, NT, BF16, false, true);
-    constexpr MmaSchedule<NPLA, NPLB> S{};
+    constexpr MmaSchedule<NPLA, NPLB, NACC> S{};
     uint32_t g = 0, it = 0;
     for (int t = blockIdx.x; t < total_tiles && !*abort_v; t += gridDim.x) {
       const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
@@ -451,30 +501,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
       const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = half * (NT / 32); c < (half + 1) * (NT / 32); ++c) {
-        uint32_t r0[16], i0[16], r1[16], i1[16];
-        tmem_ld16(tl + c * 16, r0);
-        tmem_ld16(tl + NT + c * 16, i0);
-        tmem_ld16(tl + 2 * NT + c * 16, r1);
-        tmem_ld16(tl + 3 * NT + c * 16, i1);
-        tmem_wait_ld();
-        const int col0 = n_tile * NT + c * 16;
-        if (row < cfg.M) {
-          float re0[16], re1[16], im0[16], im1[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int col = col0 + e;
-            const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
-            const float f = pow2f(ea + eb - cfg.shift);  // exact power-of-two scalings
-            const float f1 = f * cfg.w1;
-            re0[e] = __uint_as_float(r0[e]) * f;
-            im0[e] = __uint_as_float(i0[e]) * f;
-            re1[e] = __uint_as_float(r1[e]) * f1;
-            im1[e] = __uint_as_float(i1[e]) * f1;
-          }
-          epi(st, batch, row, col0, re0, re1, im0, im1);
-        }
-      }
+      for (int c = half; c < NT / 16; c += 2) epi_slice<NT, NACC>(epi, st, cfg, tl, c, batch, row, n_tile, ea, cb);
       epi.end(st, batch);
       // this warp is done reading set buf: hand it back to the MMA warp
       tc_fence_before();
@@ -511,12 +538,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // tc_gemm_persistent_kernel.  Not for epilogues that skip tiles.
 //   afull   producer -> MMA: the resident A tile has landed
 //   afree   MMA -> producer: every MMA reading the resident A has completed
-template <int NT, int KC, int NPLA, int NPLB, int NKA, int STAGES, bool BF16, class Epi>
+template <int NT, int KC, int NPLA, int NPLB, int NKA, int STAGES, bool BF16, int NACC, class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_ares_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                         GemmCfg cfg, Epi epi, int n_tiles, int m_tiles, int total_tiles) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
-  static_assert(NT % 16 == 0 && NT >= 32 && 8 * NT <= 512, "two accumulator sets must fit TMEM");
+  static_assert(NT % 16 == 0 && NT >= 32 && 4 * NACC * NT <= 512, "two accumulator sets must fit TMEM");
   static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
   extern __shared__ uint8_t smem_raw[];
@@ -537,8 +564,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (cfg.K + KC - 1) / KC;  // <= NKA, checked by the host
-  constexpr uint32_t SET = 4 * NT;
-  constexpr uint32_t TCOLS = 2 * SET;
+  constexpr uint32_t SET = 2 * NACC * NT;
+  constexpr uint32_t TCOLS = tmem_alloc_cols(2 * SET);
   const int per = (total_tiles + (int)gridDim.x - 1) / (int)gridDim.x;
   const int t_begin = (int)blockIdx.x * per;
   const int t_end = min(total_tiles, t_begin + per);
@@ -612,7 +639,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------------------------------------------------------- MMA issuer
     constexpr uint32_t id = idesc_f16(128, NT, BF16, false);
     constexpr uint32_t idn = idesc_f16(128, NT, BF16, false, true);
-    constexpr MmaSchedule<NPLA, NPLB> S{};
+    constexpr MmaSchedule<NPLA, NPLB, NACC> S{};
     uint32_t g = 0, it = 0, reloads = 0;
     int key = -1;
     for (int t = t_begin; t < t_end && !*abort_v; ++t) {
@@ -686,30 +713,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
       const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = half * (NT / 32); c < (half + 1) * (NT / 32); ++c) {
-        uint32_t r0[16], i0[16], r1[16], i1[16];
-        tmem_ld16(tl + c * 16, r0);
-        tmem_ld16(tl + NT + c * 16, i0);
-        tmem_ld16(tl + 2 * NT + c * 16, r1);
-        tmem_ld16(tl + 3 * NT + c * 16, i1);
-        tmem_wait_ld();
-        const int col0 = n_tile * NT + c * 16;
-        if (row < cfg.M) {
-          float re0[16], re1[16], im0[16], im1[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int col = col0 + e;
-            const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
-            const float f = pow2f(ea + eb - cfg.shift);
-            const float f1 = f * cfg.w1;
-            re0[e] = __uint_as_float(r0[e]) * f;
-            im0[e] = __uint_as_float(i0[e]) * f;
-            re1[e] = __uint_as_float(r1[e]) * f1;
-            im1[e] = __uint_as_float(i1[e]) * f1;
-          }
-          epi(st, batch, row, col0, re0, re1, im0, im1);
-        }
-      }
+      for (int c = half; c < NT / 16; c += 2) epi_slice<NT, NACC>(epi, st, cfg, tl, c, batch, row, n_tile, ea, cb);
       epi.end(st, batch);
       tc_fence_before();
       __syncwarp();

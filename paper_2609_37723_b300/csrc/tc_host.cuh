@@ -22,25 +22,28 @@ inline long long pad64(long long k) { return (k + 63) / 64 * 64; }
 
 int encode_planes(CUtensorMap* map, const Planes& t, int box_rows, int kc, bool bf16);
 
-// The kernel's MMA schedule is compiled for the scheme of its plane counts.
-template <int NPLA, int NPLB>
-bool products_match(const GemmCfg& cfg) {
-  using P = SchemeProducts<NPLA, NPLB>;
+// The kernel's MMA schedule is compiled for the scheme of its plane counts
+// and accumulator pairs: the caller's products must be the scheme's; the
+// accumulator of each product is the kernel's (written into cfg).
+template <int NPLA, int NPLB, int NACC>
+bool products_match(GemmCfg& cfg) {
+  using P = SchemeProducts<NPLA, NPLB, NACC>;
   bool same = cfg.nprod == P::n;
-  for (int p = 0; same && p < P::n; ++p)
-    same = cfg.pa[p] == P::pa[p] && cfg.pb[p] == P::pb[p] && cfg.acc[p] == P::acc[p];
+  for (int p = 0; same && p < P::n; ++p) same = cfg.pa[p] == P::pa[p] && cfg.pb[p] == P::pb[p];
+  for (int p = 0; same && p < P::n; ++p) cfg.acc[p] = P::acc[p];
   return same;
 }
 
-template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
-int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg,
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC = 2, class Epi>
+int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg_in,
                 int batch, const Epi& epi, cudaStream_t s) {
+  GemmCfg cfg = cfg_in;
   if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
   if (cfg.K <= 0) {
     set_error("%s: K must be positive", name);
     return DISTIL_EINVAL;
   }
-  if (!products_match<NPLA, NPLB>(cfg)) {
+  if (!products_match<NPLA, NPLB, NACC>(cfg)) {
     set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
     return DISTIL_EINVAL;
   }
@@ -49,7 +52,7 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
   DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
   constexpr size_t smem = gemm_smem_bytes<NT, KC, NPLA, NPLB, STAGES>();
   static_assert(smem <= 232448, "shared memory");
-  auto kern = tc_gemm_kernel<NT, KC, NPLA, NPLB, STAGES, BF16, Epi>;
+  auto kern = tc_gemm_kernel<NT, KC, NPLA, NPLB, STAGES, BF16, NACC, Epi>;
   static bool attr = false;
   if (!attr) {
     DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -69,15 +72,16 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
 }
 
 // Persistent launch: min(tiles, SMs) CTAs walk the 128 x NT tiles.
-template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, class Epi>
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC = 2, class Epi>
 int launch_gemm_persistent(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B,
-                           const GemmCfg& cfg, int batch, const Epi& epi, cudaStream_t s) {
+                           const GemmCfg& cfg_in, int batch, const Epi& epi, cudaStream_t s) {
+  GemmCfg cfg = cfg_in;
   if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
   if (cfg.K <= 0) {
     set_error("%s: K must be positive", name);
     return DISTIL_EINVAL;
   }
-  if (!products_match<NPLA, NPLB>(cfg)) {
+  if (!products_match<NPLA, NPLB, NACC>(cfg)) {
     set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
     return DISTIL_EINVAL;
   }
@@ -86,7 +90,7 @@ int launch_gemm_persistent(distil_ctx* ctx, const char* name, const Planes& A, c
   DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
   constexpr size_t smem = gemm_smem_bytes<NT, KC, NPLA, NPLB, STAGES>();
   static_assert(smem <= 232448, "shared memory");
-  auto kern = tc_gemm_persistent_kernel<NT, KC, NPLA, NPLB, STAGES, BF16, Epi>;
+  auto kern = tc_gemm_persistent_kernel<NT, KC, NPLA, NPLB, STAGES, BF16, NACC, Epi>;
   static bool attr = false;
   if (!attr) {
     DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -109,9 +113,10 @@ int launch_gemm_persistent(distil_ctx* ctx, const char* name, const Planes& A, c
 
 // A-resident persistent launch: K <= NKA * KC; min(tiles, SMs) CTAs, each a
 // contiguous range of tiles.
-template <int NT, int KC, int NPLA, int NPLB, int NKA, bool BF16, class Epi>
-int launch_gemm_ares(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg,
+template <int NT, int KC, int NPLA, int NPLB, int NKA, bool BF16, int NACC = 2, class Epi>
+int launch_gemm_ares(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg_in,
                      int batch, const Epi& epi, cudaStream_t s) {
+  GemmCfg cfg = cfg_in;
   using G = TileGeom<NT, KC, NPLA, NPLB>;
   constexpr size_t room = 232448 - 1024 - 256 - (size_t)NKA * G::A_STAGE;
   constexpr int ST0 = (int)(room / G::B_STAGE);
@@ -122,7 +127,7 @@ int launch_gemm_ares(distil_ctx* ctx, const char* name, const Planes& A, const P
     set_error("%s: K=%d outside (0, %d] of the resident-A kernel", name, cfg.K, NKA * KC);
     return DISTIL_EINVAL;
   }
-  if (!products_match<NPLA, NPLB>(cfg)) {
+  if (!products_match<NPLA, NPLB, NACC>(cfg)) {
     set_error("%s: split products do not match the %dx%d-plane kernel", name, NPLA, NPLB);
     return DISTIL_EINVAL;
   }
@@ -131,7 +136,7 @@ int launch_gemm_ares(distil_ctx* ctx, const char* name, const Planes& A, const P
   DISTIL_TRY(encode_planes(&mb, B, NT, KC, BF16));
   constexpr size_t smem = (size_t)NKA * G::A_STAGE + (size_t)STAGES * G::B_STAGE + 1024 + 256;
   static_assert(smem <= 232448, "shared memory");
-  auto kern = tc_gemm_ares_kernel<NT, KC, NPLA, NPLB, NKA, STAGES, BF16, Epi>;
+  auto kern = tc_gemm_ares_kernel<NT, KC, NPLA, NPLB, NKA, STAGES, BF16, NACC, Epi>;
   static bool attr = false;
   if (!attr) {
     DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -6,16 +6,21 @@ against that largest instead), and the error relative to the largest |C_ab|
 of its matrix C(p, t) ("scaled").
 
 FP16X6 is the mode that must match the FP64 oracle to 1e-6 per entry: it
-represents every row to 2^-31 of its largest entry with fixed-point slices
-(9 + 11 + 11 bits) whose leading products sum exactly in FP32, drops terms
-of relative size ~1e-8 and keeps double-float arithmetic between the
-contractions; its gate is the strict per-entry 1e-6.
+splits every row into fixed-point slices (10 + 11 + 11 bits in the mode
+contractions, 8 + 11 + 11 with eight products in the elementals) whose
+integer products sum exactly in FP32 accumulators of their own, drops
+terms below ~5e-9 of the result and keeps double-float arithmetic between
+the contractions; its gate is the strict per-entry 1e-6.
 
 The other modes are gated at matrix scale by bounds from their
-arithmetic.  BF16X6 (8 + 8 + 8 bits): each operand row holds 2^-(H+2W) =
-2^-23 of its largest entry (H = 7); a contraction of two such operands
-carries ~2 x 2^-23 x (row maximum / row rms, ~3 for Gaussian rows) ~ 7e-7,
-and C passes through four (step i, step j, source, dot): ~3e-6 -> 1e-5.
+arithmetic.  BF16X6 (8 + 8 + 8 bits, H = 7): the six kept products drop
+mid*lo, lo*mid and lo*lo, of relative size 2^-(W+2+2H) = 2^-24 of the
+largest product per term; for rows of random sign this costs about 36 x
+that relative to the result (the ratio an emulation of the FP16 split
+measures between its dropped-term bound and its error, rows of 4096), so
+~2e-6 per contraction.  C passes through five (sink and source
+elementals, step i, step j, source): ~5e-6 in quadrature, and an entry at
+a quarter of its matrix's largest doubles that at matrix scale: 3e-5.
 BF16X3 (8 + 8 bits, 2^-15 per row): ~1.5e-4 per contraction -> 1e-3.
 FP16X3 (floating h + l, 22 bits) is limited by the tensor core's FP32
 accumulation, which is not correctly rounded (measured ~2.5e-8 per
@@ -31,7 +36,7 @@ from parity import max_c_error, max_c_scaled_error, normwise
 pytestmark = pytest.mark.gpu
 
 MODES = ["fp16x6", "bf16x6", "bf16x3", "fp16x3"]
-TOL_C = {"fp16x6": 1e-6, "fp16x3": 1e-4, "bf16x6": 1e-5, "bf16x3": 1e-3}
+TOL_C = {"fp16x6": 1e-6, "fp16x3": 1e-4, "bf16x6": 3e-5, "bf16x3": 1e-3}
 
 
 def gate(mode, got, ref):
