@@ -903,10 +903,12 @@ def kernel_bytes(name, p):
     n, nb, tp = p.nv, p.nb, p.nt * p.np_
     P2 = n * (n - 1) // 2
     table = {
-        # V (nb x 6 spin pairs x n^3) and X (nb x 5 x P2 x n), complex double-float, read once
-        "dot": ((96.0 * nb * n ** 3 + 80.0 * nb * P2 * n) * tp, "V + X per (t,p), 16 B each"),
-        # the cross-product planes written once: P2 x 3 V3 x 12 B per timeslice
-        "split_pairs": (12.0 * P2 * 3 * p.V3 * p.nt, "C(N_v,2) x 3 V3 x 12 B per t written"),
+        # Z (nb x P2 x n complex double-float) read once
+        "dot": (16.0 * nb * P2 * n * tp, "Z per (t,p), 16 B per element"),
+        # V read once (nb x 6 spin pairs x n^3 x 16 B), the W planes written (nb x P2 x 5n x 12 B)
+        "split_w": ((96.0 * nb * n ** 3 + 60.0 * nb * P2 * n) * tp, "V read + W planes written per (t,p)"),
+        # the cross-product planes written once: P2 x 3 V3 x 16 B (eight 16-bit planes) per timeslice
+        "split_pairs": (16.0 * P2 * 3 * p.V3 * p.nt, "C(N_v,2) x 3 V3 x 16 B per t written"),
     }
     return table.get(name)
 
@@ -954,7 +956,8 @@ def kernel_cmacs(name, p):
     table = {
         "tc_gemm_step_i": (12.0 * nb * n ** 4 * tp, "12 N_B N_v^4 per (t,p): i contraction, 12 spin blocks, all (k,j)"),
         "tc_gemm_step_j": (24.0 * nb * n ** 4 * tp, "24 N_B N_v^4 per (t,p): j contraction, 6 spin pairs, K = 4 N_v"),
-        "tc_gemm_source": (5.0 * nb * P2 * n * n * tp, "5 N_B C(N_v,2) N_v^2 per (t,p): k' contraction"),
+        "tc_gemm_tcontract": (5.0 * nb * P2 * n * n * tp,
+                              "5 N_B C(N_v,2) N_v^2 per (t,p): T^c contraction of W, K = 5 N_v"),
         "tc_gemm_elementals": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p): useful i<j<k MACs"),
         "elementals_simt_f32": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p)"),
         "elementals_simt_f64": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p)"),
@@ -965,16 +968,10 @@ def kernel_cmacs(name, p):
 
 
 # DRAM bytes (read + write) per launch from ncu's dram__bytes_* counters of
-# each tensor-core kernel family on the workload L32_Nt64_Nv128 (profiles/,
-# first two timeslices: the per-launch units are those of the full size).
-# Only valid for that workload and these kernels.
-TRAFFIC_L32_NV128 = {
-    "tc_gemm_elementals": 476.6e6 + 0.4e6,
-    "tc_gemm_step_i": 696.4e6 + 1939.9e6,
-    "tc_gemm_step_j": 625.1e6 + 353.5e6,
-    "tc_gemm_source": 78.5e6 + 442.0e6,
-    "dot": 1698.1e6 + 1.2e6,
-}
+# each kernel family on the workload L32_Nt64_Nv128 (first two timeslices:
+# the per-launch units are those of the full size), for the kernels as they
+# stand; empty when they changed after the last capture.
+TRAFFIC_L32_NV128 = {}
 
 
 def roofline(dom, kstats, p, mode, pk, steps):

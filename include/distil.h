@@ -260,13 +260,16 @@ int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* p
 /* ------------------------------------------------------------------ */
 
 /* Tensor-core kernel variant of each mode-contraction site of the mixed
- * correlator, variants[3] = {step i, step j, source}: 0 = one 128 x 128
- * tile per CTA, 1 = persistent CTAs with two 128 x 64 accumulator sets,
- * 2 (step i only) = persistent with the whole-K A tile resident in shared
- * memory (used when N_v <= 128, else variant 1).
- * Every variant gives identical results; only the speed differs.  The
- * defaults are {1, 0, 1}.  The library has no counterpart of this in the
- * paper: it is a property of this implementation. */
+ * correlator, variants[3] = {step i (K = N_v), step j (K = 4 N_v), the T
+ * contraction Z = W T^c of the final sum (K = 5 N_v)}: 0 = one 128 x NT
+ * tile per CTA (NT = 128, or 80 / 64 at the sites that keep three
+ * accumulator pairs), 1 = persistent CTAs with two accumulator sets
+ * (128 x 64, or 128 x 32 with three pairs), 2 (step i only) = persistent
+ * with the whole-K A tile resident in shared memory (used when N_v <= 128,
+ * else variant 1).  Every variant of a site gives identical results; only
+ * the speed differs.  The defaults are {1, 0, 0}.  The library has no
+ * counterpart of this in the paper: it is a property of this
+ * implementation. */
 int distil_set_tuning(distil_ctx* ctx, const int* variants);
 int distil_get_tuning(const distil_ctx* ctx, int* variants);
 

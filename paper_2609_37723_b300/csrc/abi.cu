@@ -64,7 +64,7 @@ int distil_create(int device, distil_ctx** out) {
   c->prof = new Profiler();
   c->tune[0] = 1;  // step i (K = N_v): persistent, epilogue overlapped (2 measured slower at N_v = 128)
   c->tune[1] = 0;  // step j (K = 4 N_v): one 128 x 128 tile per CTA
-  c->tune[2] = 1;  // source (K = N_v): persistent
+  c->tune[2] = 0;  // T contraction (K = 5 N_v, three accumulator pairs): one tile per CTA
   if (cudaMalloc(&c->d_error, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMemset(c->d_error, 0, sizeof(unsigned int) * 4) != cudaSuccess) {
     set_error("distil_create: cannot allocate the device error word");

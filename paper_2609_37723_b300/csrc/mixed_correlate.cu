@@ -13,15 +13,17 @@
 // Per (t, p):
 //   split    Aa  rows (a'beta, i')  K i        from Gamma_beta tau[(alpha(beta) i)][(a' i')]
 //            tauT rows (b' j')      K (beta j) from tau[(beta j)][(b' j')]
-//            Tc  rows (c, k)        K k'       from the five source blocks
+//            TcT rows k'            K (c, k)   from the five source blocks T^c[k][k']
 //            G   rows (a, (k,j))    K i        from g g g Phi_snk
-//            S   rows (b, i'<j')    K k'       from g g g conj(Phi_src)
 //   step i   U[a][a'][(i',k)][(beta,j)] = sum_i Aa G, split by the epilogue
 //            with the row exponent of the Cauchy-Schwarz bound
 //            |U| <= max_beta |Aa row| * max_j |G row|
 //   step j   V[a][slot][j'][(i',k)]     = sum_(beta,j) U tauT
-//   source   X[b][c][pair][k]           = sum_k' S Tc
-//   dot      C_ab
+//   split    W rows (a, i'<j')      K (c, k)   the source-weighted antisymmetric
+//                                              parts w^a_c of V (correlate.cuh)
+//   T contr. Z[a][pair][k']         = sum_(c,k) W TcT
+//   dot      C_ab = sum_(pair,k') Z^a gamma^b conj(Phi_src~), with
+//            gamma^b = g^b_i' g^b_j' g^b_k' the only b-dependence
 #include "correlate.cuh"
 #include "df.cuh"
 #include "mixed.cuh"
@@ -137,6 +139,11 @@ struct TcSrc {  // rows c*n + k, K = k': T^c[k][k']
     return make_float2(v.re.hi, v.im.hi);
   }
 };
+struct TcTSrc {  // rows k', K = (c, k): T^c[k][k'] (TcSrc transposed)
+  TcSrc tc;
+  __device__ __forceinline__ CDF operator()(long long kp, int kk) const { return tc(kk, (int)kp); }
+  __device__ __forceinline__ float2 approx(long long kp, int kk) const { return tc.approx(kk, (int)kp); }
+};
 // sorted-triple lookup with sign; 0 on a repeated index
 __device__ __forceinline__ CDF phi_at(const CDF* phi, int i, int j, int k, DF w) {
   if (i == j || j == k || i == k) return cdf_zero();
@@ -173,33 +180,6 @@ struct GSrc {  // rows a*n^2 + k*n + j, K = i: g_i g_j g_k Phi_ijk
     return make_float2(p.re.hi * w, p.im.hi * w);
   }
 };
-struct SSrc {  // rows b*P2 + pair(i'<j'), K = k': g g g conj(Phi_{i'j'k'})
-  const CDF* phi;
-  const DF* g;
-  int n;
-  long long P2;
-  __device__ __forceinline__ CDF operator()(long long r, int kp) const {
-    const int b = (int)(r / P2);
-    int ip, jp;
-    pair_unrank(r % P2, ip, jp);
-    const DF* gb = g + (long long)b * n;
-    return cdf_conj(phi_at(phi, ip, jp, kp, df_mul(df_mul(gb[ip], gb[jp]), gb[kp])));
-  }
-  __device__ __forceinline__ float2 approx(long long r, int kp) const {
-    const int b = (int)(r / P2);
-    int ip, jp;
-    pair_unrank(r % P2, ip, jp);
-    if (kp == ip || kp == jp) return make_float2(0.f, 0.f);
-    int x = ip, y = jp, z = kp;
-    if (y > z) { int t = y; y = z; z = t; }
-    if (x > y) { int t = x; x = y; y = t; }
-    const DF* gb = g + (long long)b * n;
-    const float w = gb[ip].hi * gb[jp].hi * gb[kp].hi;
-    const CDF p = phi[triple_rank(x, y, z)];
-    return make_float2(p.re.hi * w, p.im.hi * w);
-  }
-};
-
 // mG[a*n + k] = max_j |G row (a, k, j)| (one warp per (a, k)).
 __global__ void g_rowmax_kernel(const float* __restrict__ nG, int n, int nb, float* __restrict__ mG) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -303,75 +283,165 @@ __device__ __forceinline__ void df_acc_prod(float& s, float& c, DF a, DF b) {
   c += t.lo + __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
 }
 
-// C[q][a][b][t] += 2^scale sum_terms coef sum_{i'<j',k} (V^a_{j'i'k} - V^a_{i'j'k}) X^{b,c}_{pair,k}
-// V[a][slot][j'][i'][k], X[b][c][pair][k] (double-floats).  Warp w of a
-// block takes a = w and 32 consecutive (pair, k) elements per iteration, so
-// the nb warps of a block read the same X values and all but the first find
-// them in L1: X leaves HBM once per launch.  The two terms that share a
-// source matrix are summed before the product.
 __device__ __forceinline__ CDF ldg_cdf(const CDF* p) {  // p is 16-byte aligned
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
   return cdf_make(df_make(v.x, v.y), df_make(v.z, v.w));
 }
+
+// W^a[pair][(c, k)] = w^a_c[pair][k], the combinations of the antisymmetric
+// parts d_s[pair][k] = V^a_{j'i'k} - V^a_{i'j'k} of the sink spin slots s
+// that meet source matrix c (correlate.cuh: coefficients -3, -2 on matrix 0,
+// +-1 on the others), split into NPC fixed-point pieces with one exponent
+// per row (a, pair).  One block per row, thread tid takes k = tid + 256 u.
+//   out[a][plane][pair][c n + k]  (plane stride P2 ld, a stride NPL P2 ld)
+template <bool BF16, bool FIXED, int NPC, int PER>
+__global__ void __launch_bounds__(256) split_w_kernel(const CDF* __restrict__ V, int nv, long long P2, int H,
+                                                      typename tc::Piece<BF16>::T* __restrict__ out, long long ld,
+                                                      int* __restrict__ exps) {
+  using P16 = typename tc::Piece<BF16>::T;
+  __shared__ float red[8];
+  __shared__ int sh_e;
+  const long long r = blockIdx.x;
+  const int a = (int)(r / P2);
+  const long long pair = r - (long long)a * P2;
+  int ip, jp;
+  pair_unrank(pair, ip, jp);
+  const long long n = nv, n3 = n * n * n;
+  const CDF* Va = V + (long long)a * NPAIR * n3;
+  const long long o1 = ((long long)jp * n + ip) * n, o2 = ((long long)ip * n + jp) * n;
+  CDF w[PER][NSRC];
+  float m = 0.f;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int k = threadIdx.x + 256 * u;
+    if (k < nv) {
+      CDF d[NTERM];
+#pragma unroll
+      for (int t = 0; t < NTERM; ++t) {
+        const CDF* Vs = Va + dot_slot(t) * n3;
+        const CDF v1 = ldg_cdf(Vs + o1 + k), v2 = ldg_cdf(Vs + o2 + k);
+        d[t] = cdf_make(df_sub_fast(v1.re, v2.re), df_sub_fast(v1.im, v2.im));
+      }
+      static_assert(dot_coef(0) == -3.0 && dot_coef(1) == -2.0 && dot_src(0) == 0 && dot_src(1) == 0,
+                    "source-0 terms");
+      static_assert(dot_coef(2) == -1.0 && dot_coef(3) == 1.0 && dot_coef(4) == -1.0 && dot_coef(5) == 1.0,
+                    "unit coefficients");
+      // w_0 = -3 d_0 - 2 d_1 = -(2 (d_0 + d_1) + d_0); w_c = coef_t d_t for the others
+      const DF sr = df_add(d[0].re, d[1].re), si = df_add(d[0].im, d[1].im);
+      w[u][0] = cdf_make(df_neg(df_add(df_make(2.f * sr.hi, 2.f * sr.lo), d[0].re)),
+                         df_neg(df_add(df_make(2.f * si.hi, 2.f * si.lo), d[0].im)));
+#pragma unroll
+      for (int t = 2; t < NTERM; ++t)
+        w[u][dot_src(t)] = dot_coef(t) > 0 ? d[t] : cdf_make(df_neg(d[t].re), df_neg(d[t].im));
+#pragma unroll
+      for (int c = 0; c < NSRC; ++c) m = fmaxf(m, fmaxf(fabsf(w[u][c].re.hi), fabsf(w[u][c].im.hi)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < 8; ++i) m = fmaxf(m, red[i]);
+    m = fmaxf(m, red[0]);
+    sh_e = row_exponent(m * (1.f + 1.f / 65536.f));
+    exps[r] = sh_e;
+  }
+  __syncthreads();
+  const Pow2 sc = pow2_pair(H - sh_e);
+  const long long ps = P2 * ld;
+  P16* base = out + (long long)a * (2 * NPC) * ps + pair * ld;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int k = threadIdx.x + 256 * u;
+    if (k >= nv) break;
+#pragma unroll
+    for (int c = 0; c < NSRC; ++c) {
+      P16 pr[NPC], pi[NPC];
+      make_pieces<BF16, FIXED, NPC>(w[u][c].re, sc, pr);
+      make_pieces<BF16, FIXED, NPC>(w[u][c].im, sc, pi);
+      const long long kk = (long long)c * nv + k;
+#pragma unroll
+      for (int q = 0; q < NPC; ++q) {
+        base[(2 * q) * ps + kk] = pr[q];
+        base[(2 * q + 1) * ps + kk] = pi[q];
+      }
+    }
+  }
+}
+
 // Each block leaves its partial sums in part[block][a][b] (FP64); a second
 // kernel adds the blocks in a fixed order, so C is the same to the last bit
 // from run to run (and graph replay to replay).
 constexpr int DOT_BLOCKS = 1184;  // 8 x 148 SMs
+
+// C_ab partial sums over the elements e = (pair i'<j', k') of
+//   sum_e gamma^b[e] (Z^a[e] conj(Phi~[e])),  gamma^b = g^b_i' g^b_j' g^b_k',
+// Phi~[e] = the source elemental at the sorted (i', j', k') with the sign of
+// the sort (0 if k' is i' or j').  A block of 32 nb threads takes tiles of
+// 32 nb elements: first every thread forms conj(Phi~) and the nb weights
+// gamma^b of one element into shared memory, then warp a runs over the tile
+// with a = its warp, one element per lane at a time, keeping the nb complex
+// sums C_ab as unevaluated double-floats.
 template <int MAXB>
 __global__ void __launch_bounds__(32 * MAXB)
-dot_df_kernel(const CDF* __restrict__ V, const CDF* __restrict__ X, int nv, int nb, Cx<double>* __restrict__ part) {
+dot_z_kernel(const CDF* __restrict__ Z, const CDF* __restrict__ phi, const DF* __restrict__ g, int nv, int nb,
+             Cx<double>* __restrict__ part) {
+  __shared__ CDF sphi[32 * MAXB];
+  __shared__ DF sgam[MAXB][32 * MAXB];
+  const int tile = 32 * nb;
   const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (a >= nb) return;
   const long long P2 = comb2(nv);
-  const long long n3 = (long long)nv * nv * nv;
   const long long work = P2 * nv;
   float sr[MAXB], cr[MAXB], si[MAXB], ci[MAXB];
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) sr[b] = cr[b] = si[b] = ci[b] = 0.f;
-  const CDF* Va = V + (long long)a * NPAIR * n3;
-  for (long long e = blockIdx.x * 32LL + lane; e < work; e += (long long)gridDim.x * 32) {
-    const long long q = e / nv;
-    const int k = (int)(e - q * nv);
-    int ip, jp;
-    pair_unrank(q, ip, jp);
-    const long long o1 = ((long long)jp * nv + ip) * nv + k, o2 = ((long long)ip * nv + jp) * nv + k;
-    // d_t = V_{j'i'k} - V_{i'j'k} of the term's slot; the coefficients are
-    // -3, -2 (both on source 0) and +-1: w_0 = -(2 (d_0 + d_1) + d_0),
-    // w_c = coef_t d_t for the other sources (a sign, no product)
-    CDF d[NTERM];
+  const CDF* Za = Z + (long long)a * work;
+  for (long long e0 = (long long)blockIdx.x * tile; e0 < work; e0 += (long long)gridDim.x * tile) {
+    {  // phase 1: one element per thread
+      const long long e = e0 + threadIdx.x;
+      CDF f = cdf_zero();
+      DF gm[MAXB];
 #pragma unroll
-    for (int t = 0; t < NTERM; ++t) {
-      const CDF* Vs = Va + dot_slot(t) * n3;
-      const CDF v1 = ldg_cdf(Vs + o1), v2 = ldg_cdf(Vs + o2);
-      d[t] = cdf_make(df_sub_fast(v1.re, v2.re), df_sub_fast(v1.im, v2.im));
+      for (int b = 0; b < MAXB; ++b) gm[b] = df_make(0.f, 0.f);
+      if (e < work) {
+        const long long pair = e / nv;
+        const int kp = (int)(e - pair * nv);
+        int ip, jp;
+        pair_unrank(pair, ip, jp);
+        if (kp != ip && kp != jp) {
+          f = cdf_conj(phi_at(phi, ip, jp, kp, df_make(1.f, 0.f)));
+#pragma unroll
+          for (int b = 0; b < MAXB; ++b) {
+            if (b >= nb) break;
+            const DF* gb = g + (long long)b * nv;
+            gm[b] = df_mul(df_mul(gb[ip], gb[jp]), gb[kp]);
+          }
+        }
+      }
+      sphi[threadIdx.x] = f;
+#pragma unroll
+      for (int b = 0; b < MAXB; ++b)
+        if (b < nb) sgam[b][threadIdx.x] = gm[b];
     }
-    static_assert(dot_coef(0) == -3.0 && dot_coef(1) == -2.0 && dot_src(0) == 0 && dot_src(1) == 0,
-                  "source-0 terms");
-    CDF w[NSRC];
-    {
-      const DF sr = df_add_fast(d[0].re, d[1].re), si = df_add_fast(d[0].im, d[1].im);
-      w[0] = cdf_make(df_neg(df_add_fast(df_make(2.f * sr.hi, 2.f * sr.lo), d[0].re)),
-                      df_neg(df_add_fast(df_make(2.f * si.hi, 2.f * si.lo), d[0].im)));
-    }
+    __syncthreads();
+    // phase 2: warp a over the tile
+    for (int i = lane; i < tile; i += 32) {
+      const long long e = e0 + i;
+      if (e >= work) break;
+      const CDF z = ldg_cdf(Za + e);
+      const CDF f = sphi[i];
+      // u = z f (complex double-float product)
+      const DF ur = df_sub(df_mul(z.re, f.re), df_mul(z.im, f.im));
+      const DF ui = df_add(df_mul(z.re, f.im), df_mul(z.im, f.re));
 #pragma unroll
-    for (int t = 2; t < NTERM; ++t) {
-      static_assert(dot_coef(2) == -1.0 && dot_coef(3) == 1.0 && dot_coef(4) == -1.0 && dot_coef(5) == 1.0,
-                    "unit coefficients");
-      w[dot_src(t)] = dot_coef(t) > 0 ? d[t] : cdf_make(df_neg(d[t].re), df_neg(d[t].im));
-    }
-#pragma unroll
-    for (int b = 0; b < MAXB; ++b) {
-      if (b >= nb) break;
-      const CDF* Xb = X + (long long)b * NSRC * work + e;
-#pragma unroll
-      for (int c = 0; c < NSRC; ++c) {
-        const CDF x = ldg_cdf(Xb + c * work);
-        df_acc_prod(sr[b], cr[b], w[c].re, x.re);
-        df_acc_prod(sr[b], cr[b], df_neg(w[c].im), x.im);
-        df_acc_prod(si[b], ci[b], w[c].re, x.im);
-        df_acc_prod(si[b], ci[b], w[c].im, x.re);
+      for (int b = 0; b < MAXB; ++b) {
+        if (b >= nb) break;
+        const DF gb = sgam[b][i];
+        df_acc_prod(sr[b], cr[b], gb, ur);
+        df_acc_prod(si[b], ci[b], gb, ui);
       }
     }
+    __syncthreads();
   }
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) {
@@ -424,14 +494,14 @@ dot_reduce_kernel(const Cx<double>* __restrict__ part, int nblocks, int nb, cons
 
 // ------------------------------------------------------------------ workspace
 struct MixedWs {
-  void *Aa, *TT, *Tc, *G, *S, *U;
-  int *eAa, *eTT, *eTc, *eG, *eS, *eU;
+  void *Aa, *TT, *TcT, *G, *U, *W;
+  int *eAa, *eTT, *eTcT, *eG, *eU, *eW;
   float *nAa, *nG, *mG;
-  CDF *V, *X, *phs, *ph0;
+  CDF *V, *Z, *phs, *ph0;
   Cx<double>* part;
   DF* g;
   int *etau, *esnk, *esrc;
-  long long ldn, ld4;
+  long long ldn, ld4, ld5;
 };
 
 static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, int nb) {
@@ -440,24 +510,25 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, 
   MixedWs w;
   w.ldn = tc::pad64(n);
   w.ld4 = tc::pad64(4 * n);
+  w.ld5 = tc::pad64((long long)NSRC * n);
   w.Aa = ar.take<uint16_t>(12LL * npa * n * w.ldn);
   w.TT = ar.take<uint16_t>((long long)npb * 4 * n * w.ld4);
-  w.Tc = ar.take<uint16_t>(5LL * npb * n * w.ldn);
+  w.TcT = ar.take<uint16_t>((long long)npb * n * w.ld5);
   w.G = ar.take<uint16_t>((long long)nb * npb * n2 * w.ldn);
-  w.S = ar.take<uint16_t>((long long)nb * npa * P2 * w.ldn);
   w.U = ar.take<uint16_t>((long long)nb * 3 * npa * n2 * w.ld4);
+  w.W = ar.take<uint16_t>((long long)nb * npa * P2 * w.ld5);
   w.eAa = ar.take<int>(12 * n);
   w.eTT = ar.take<int>(4 * n);
-  w.eTc = ar.take<int>(5 * n);
+  w.eTcT = ar.take<int>(n);
   w.eG = ar.take<int>(nb * n2);
-  w.eS = ar.take<int>(nb * P2);
   w.eU = ar.take<int>(3 * nb * n2);
+  w.eW = ar.take<int>(nb * P2);
   w.nAa = ar.take<float>(12 * n);
   w.nG = ar.take<float>(nb * n2);
   w.mG = ar.take<float>(nb * n);
   w.V = ar.take<CDF>((long long)nb * NPAIR * n3);
   w.part = ar.take<Cx<double>>((long long)DOT_BLOCKS * nb * nb);
-  w.X = ar.take<CDF>((long long)nb * NSRC * P2 * n);
+  w.Z = ar.take<CDF>((long long)nb * P2 * n);
   w.phs = ar.take<CDF>(T3);
   w.ph0 = ar.take<CDF>(T3);
   w.g = ar.take<DF>((long long)(nt + 1) * nb * n);
@@ -474,14 +545,16 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
 }
 
 // Mode-contraction GEMM in the kernel variant the context's tuning table
-// names for this site: 0 = one 128 x NT tile per CTA (wide MMAs, no overlap
+// names for this site (step i, step j, and the T contraction, which the
+// tuning table and the ABI call the "source" site: it replaced the
+// source-side contraction and has its K = 5 N_v): 0 = one 128 x NT tile per CTA (wide MMAs, no overlap
 // of epilogue and MMAs), 1 = persistent CTAs with two accumulator sets (the
 // epilogue of one tile overlaps the MMAs of the next), 2 = the same with the
 // whole-K A tile resident in shared memory across the column tiles of a
 // batch (K <= 128; else variant 1).  NACC is a property of the site, not of
-// the variant: step j (K = 4 N_v) accumulates the 6-product schemes in three
-// pairs (exact cross terms; the second-order terms drift with K otherwise),
-// the short contractions (K = N_v) in two.  All variants of a site
+// the variant: step j (K = 4 N_v) and the T contraction (K = 5 N_v)
+// accumulate the 6-product schemes in three pairs (exact cross terms; the
+// second-order terms drift with K otherwise), step i (K = N_v) in two.  All variants of a site
 // accumulate every element over K in the same order into the same pairs, so
 // they give identical results.
 enum GemmSite { SITE_STEP_I = 0, SITE_STEP_J = 1, SITE_SOURCE = 2 };
@@ -503,9 +576,20 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& 
     return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16, NACC>(
         ctx, name, A, B, cfg, batch, epi, s);
   }
-  if (cfg.N > 64)
+  if (cfg.N > 64) {
+    if constexpr (NACC == 3) {
+      // 80-wide tiles read A once per 80 columns, 64-wide ones waste no
+      // padding when N is a multiple of 64: shared-memory reads per output
+      // ~ padded columns x (1/NT + 1/128)
+      const double c80 = ((cfg.N + 79) / 80) * 80 * (1.0 / 80 + 1.0 / 128);
+      const double c64 = ((cfg.N + 63) / 64) * 64 * (1.0 / 64 + 1.0 / 128);
+      if (c64 < c80)
+        return tc::launch_gemm<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16, NACC>(
+            ctx, name, A, B, cfg, batch, epi, s);
+    }
     return tc::launch_gemm<NTW, KC, NPLA, NPLB, tc::max_stages<NTW, KC, NPLA, NPLB>(), BF16, NACC>(
         ctx, name, A, B, cfg, batch, epi, s);
+  }
   if (cfg.N > 32)
     return tc::launch_gemm<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16, NACC>(ctx, name, A, B, cfg,
                                                                                                 batch, epi, s);
@@ -532,9 +616,8 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
   const int H = sch.H;
   DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_tau", AaSrc{tau, etau, nv}, 12 * n, n, nv, H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
   DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TTSrc{tau, etau, nv}, 4 * n, 4 * n, 4 * nv, H, w.TT, w.ld4, w.eTT, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcSrc{tau, etau, nv}, 5 * n, n, nv, H, w.Tc, w.ldn, w.eTc, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcTSrc{TcSrc{tau, etau, nv}}, n, n, NSRC * nv, H, w.TcT, w.ld5, w.eTcT, s)));
   DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_sink", GSrc{w.phs, g_snk, nv}, nb * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_source", SSrc{w.ph0, g_src, nv, P2}, nb * P2, P2, nv, H, w.S, w.ldn, w.eS, s)));
   {
     Launch L(ctx, "u_exponent", s);
     g_rowmax_kernel<<<nblk(32LL * nb * n), 256, 0, s>>>(w.nG, nv, nb, w.mG);
@@ -556,19 +639,6 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
     DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
   }
-  // ---- source: batch (b, c) = nb x 5; X[b][c][pair][k]
-  {
-    Planes A = planes_of(w.S, n, P2, nb, NPLA, w.ldn);
-    Planes B = planes_of(w.Tc, n, n, NSRC, NPLB, w.ldn);
-    cfg.M = (int)P2; cfg.N = nv; cfg.K = nv;
-    cfg.a = tc::OpMap{NSRC, nb, 1, 0, 0, (int)P2, w.eS};
-    cfg.b = tc::OpMap{1, NSRC, 1, 0, 0, nv, w.eTc};
-    EpiStoreCDF epi;
-    epi.out = w.X;
-    epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
-    epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_SOURCE, "tc_gemm_source", A, B, cfg, nb * NSRC, epi, s)));
-  }
   // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
   for (int ap = 0; ap < 3; ++ap) {
@@ -583,16 +653,42 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
     DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
   }
+  // ---- W: the source-weighted antisymmetric parts of V, split (rows (a, pair), K = (c, k))
+  {
+    Launch L(ctx, "split_w", s);
+    auto* wout = reinterpret_cast<P16*>(w.W);
+    if (nv <= 256)
+      split_w_kernel<BF16, FIXED, NA, 1><<<(unsigned)(nb * P2), 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+    else if (nv <= 512)
+      split_w_kernel<BF16, FIXED, NA, 2><<<(unsigned)(nb * P2), 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+    else
+      split_w_kernel<BF16, FIXED, NA, 4><<<(unsigned)(nb * P2), 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+  }
+  DISTIL_LAUNCH_CHECK();
+  // ---- T contraction: Z[a][pair][k'] = sum_(c,k) W[a][pair][(c,k)] T^c[k][k'] (K = 5 N_v)
+  {
+    Planes A = planes_of(w.W, NSRC * n, P2, nb, NPLA, w.ld5);
+    Planes B = planes_of(w.TcT, NSRC * n, n, 1, NPLB, w.ld5);
+    cfg.M = (int)P2; cfg.N = nv; cfg.K = NSRC * nv;
+    cfg.a = tc::OpMap{1, nb, 1, 0, 0, (int)P2, w.eW};
+    cfg.b = tc::OpMap{1, 1, 0, 0, 0, nv, w.eTcT};
+    EpiStoreCDF epi;
+    epi.out = w.Z;
+    epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
+    epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_SOURCE, "tc_gemm_tcontract", A, B, cfg, nb, epi, s)));
+  }
   // ---- dot
   {
     const long long work = P2 * n;
-    unsigned gx = (unsigned)((work + 31) / 32);
+    const long long tile = 32LL * nb;
+    unsigned gx = (unsigned)((work + tile - 1) / tile);
     if (gx > (unsigned)DOT_BLOCKS) gx = DOT_BLOCKS;
     Launch L(ctx, "dot", s);
     if (nb <= 8)
-      dot_df_kernel<8><<<gx, 32 * 8, 0, s>>>(w.V, w.X, nv, nb, w.part);
+      dot_z_kernel<8><<<gx, 32 * nb, 0, s>>>(w.Z, w.ph0, g_src, nv, nb, w.part);
     else
-      dot_df_kernel<16><<<gx, 32 * 16, 0, s>>>(w.V, w.X, nv, nb, w.part);
+      dot_z_kernel<16><<<gx, 32 * nb, 0, s>>>(w.Z, w.ph0, g_src, nv, nb, w.part);
     dot_reduce_kernel<<<nb * nb, 256, 0, s>>>(w.part, (int)gx, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
   }
   DISTIL_LAUNCH_CHECK();

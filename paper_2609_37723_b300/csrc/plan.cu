@@ -82,7 +82,7 @@ int time_sites(distil_ctx* ctx, const distil_batch_shape* sh, const distil_batch
   DISTIL_TRY(distil_profile_read(ctx, nullptr, 0, &n));
   std::vector<distil_kernel_stat> st(n > 0 ? n : 1);
   DISTIL_TRY(distil_profile_read(ctx, st.data(), n, &n));
-  static const char* names[3] = {"tc_gemm_step_i", "tc_gemm_step_j", "tc_gemm_source"};
+  static const char* names[3] = {"tc_gemm_step_i", "tc_gemm_step_j", "tc_gemm_tcontract"};
   for (int k = 0; k < 3; ++k) {
     ms[k] = 0.0;
     for (int i = 0; i < n; ++i)

@@ -360,7 +360,7 @@ def profile_read(device: int = 0) -> dict:
 # ------------------------------------------------------------------ tuning and batched plans
 
 def set_tuning(variants, device: int = 0):
-    """Kernel variant of each mode-contraction site {step i, step j, source}:
+    """Kernel variant of each mode-contraction site {step i, step j, T contraction}:
     0 = one 128 x 128 tile per CTA, 1 = persistent, overlapped epilogue,
     2 (step i only) = persistent with the A tile resident in shared memory."""
     arr = (ctypes.c_int * 3)(*[int(x) for x in variants])

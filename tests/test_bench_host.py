@@ -26,7 +26,7 @@ def test_kernel_rooflines_from_event_times():
     assert j["frac"] == pytest.approx(j["achieved"] / 1000.0)
     d = rows["dot"]
     P2 = n * (n - 1) // 2
-    assert d["bound"] == "hbm" and d["achieved"] == pytest.approx((96.0 * nb * n ** 3 + 80.0 * nb * P2 * n) * tp / 1e9)
+    assert d["bound"] == "hbm" and d["achieved"] == pytest.approx(16.0 * nb * P2 * n * tp / 1e9)
     assert bench.kernel_rooflines(ks, p, "fp32", pk, 1) == []
 
 
