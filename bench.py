@@ -557,6 +557,9 @@ def run_timeslices(args):
     ws = torch.empty(max(ws_e, ws_c, 1), dtype=torch.uint8, device=dev)
     log(f"device: v {v.numel() * v.element_size() / 1e9:.1f} GB, workspace {ws.numel() / 1e9:.1f} GB")
 
+    if args.tuning:
+        distil.set_tuning([int(x) for x in args.tuning.split(",")], device=local)
+
     def step(t, vt, taut):
         distil.elementals(vt, p.L, p.mom, mode, out=phi_t, workspace=ws)
         distil.correlate_slice(phi_t[0], phi_src[0], taut, prof, prof, C, t, mode, workspace=ws)
@@ -671,6 +674,7 @@ def run_timeslices(args):
             "roofline": roof,
             "kernel_rooflines": kernel_rooflines(kstats, p1, mode, pk, args.steps),
             "whole_step": whole_step_tensor(kstats, p1, mode, pk, args.steps, ms_step),
+            "tuning": distil.get_tuning(device=local),
             "clocks": clk,
             "parity": parity,
             "cpu_baseline": cpu,
@@ -1114,6 +1118,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32/FP64 comparison")
     ap.add_argument("--ncfg", type=int, default=4,
                     help="workload 4: configurations in the ensemble (16 in full; each holds 3-6 GB of inputs)")
+    ap.add_argument("--tuning", default="",
+                    help="kernel variants of the three contraction sites, e.g. 0,0,0 (default: the library's)")
     ap.add_argument("--nt", type=int, default=0,
                     help="keep only the first NT timeslices (profiling a smaller case; not a bench number)")
     args = ap.parse_args()

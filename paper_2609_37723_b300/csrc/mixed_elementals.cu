@@ -57,84 +57,29 @@ struct MomArgs {
   int mom[EL_MAX_MOM][3];
 };
 
-// Cross-product operand of one K chunk, split into NPC fixed-point pieces:
-// one block per pair q = (j, k) (j-major order), each thread a few sites x
-// of the chunk [x0, x0 + nx): the three colour components of w = v_j x v_k at
-// a site are formed together from the six loaded values (exactly, as
-// double-floats), the row's exponent comes from the exact maximum over the
-// chunk (block reduction), and the pieces go to
-//   out[plane][q][3 (x - x0) + a]   (plane = 2 piece + re/im, stride P2 ld).
-constexpr int SP_THREADS = 512;
-constexpr int SP_SITES = (EL_KC / 3 + SP_THREADS - 1) / SP_THREADS;  // sites per thread
-template <bool BF16, bool FIXED, int NPC>
-__global__ void __launch_bounds__(SP_THREADS) split_pairs_kernel(const float2* __restrict__ v, const int2* __restrict__ pairs,
-                                                                 long long V3, long long x0, int nx, int H,
-                                                                 typename tc::Piece<BF16>::T* __restrict__ out,
-                                                                 long long ld, long long P2, int* __restrict__ exps) {
-  using P16 = typename tc::Piece<BF16>::T;
-  __shared__ float red[SP_THREADS / 32];
-  __shared__ int sh_e;
-  const long long q = blockIdx.x;
-  const int2 jk = pairs[q];
-  const float2* vj = v + (long long)jk.x * V3 * 3;
-  const float2* vk = v + (long long)jk.y * V3 * 3;
-  CDF w[SP_SITES][3];
-  float m = 0.f;
-#pragma unroll
-  for (int u = 0; u < SP_SITES; ++u) {
-    const int xl = threadIdx.x + SP_THREADS * u;
-    if (xl < nx) {
-      const long long x = x0 + xl;
-      float2 a[3], b[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        a[c] = vj[x * 3 + c];
-        b[c] = vk[x * 3 + c];
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        // w^c = v_j^(c+1) v_k^(c+2) - v_j^(c+2) v_k^(c+1)  (indices mod 3)
-        const float2 jb = a[(c + 1) % 3], jc = a[(c + 2) % 3], kb = b[(c + 1) % 3], kc = b[(c + 2) % 3];
-        w[u][c] = cdf_make(dot4(jb.x, kc.x, -jb.y, kc.y, -jc.x, kb.x, jc.y, kb.y),
-                           dot4(jb.x, kc.y, jb.y, kc.x, -jc.x, kb.y, -jc.y, kb.x));
-        m = fmaxf(m, fmaxf(fabsf(w[u][c].re.hi), fabsf(w[u][c].im.hi)));
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) w[u][c] = cdf_zero();
-    }
+struct WSrc {  // rows q (pairs), K = (x, a) from K0 (3 V3 < 2^31)
+  const float2* v;  // v[t] = [n][V3][3]
+  const int2* pairs;
+  long long V3;
+  int K0;
+  __device__ __forceinline__ CDF operator()(long long q, int kk) const {
+    const int K = K0 + kk;
+    const int x = K / 3, a = K - 3 * x;
+    const int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+    const int2 jk = pairs[q];
+    const float2* vj = v + ((long long)jk.x * V3 + x) * 3;
+    const float2* vk = v + ((long long)jk.y * V3 + x) * 3;
+    const float2 jb = vj[b], jc = vj[c], kb = vk[b], kc = vk[c];
+    // w^a = v_j^b v_k^c - v_j^c v_k^b, exactly as a double-float
+    const DF re = dot4(jb.x, kc.x, -jb.y, kc.y, -jc.x, kb.x, jc.y, kb.y);
+    const DF im = dot4(jb.x, kc.y, jb.y, kc.x, -jc.x, kb.y, -jc.y, kb.x);
+    return cdf_make(re, im);
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < SP_THREADS / 32; ++i) m = fmaxf(m, red[i]);
-    m = fmaxf(m, red[0]);
-    sh_e = row_exponent(m * (1.f + 1.f / 65536.f));
-    exps[q] = sh_e;
+  __device__ __forceinline__ float2 approx(long long q, int kk) const {
+    const CDF z = (*this)(q, kk);
+    return make_float2(z.re.hi, z.im.hi);
   }
-  __syncthreads();
-  const Pow2 sc = pow2_pair(H - sh_e);
-  const long long ps = P2 * ld;
-  P16* base = out + q * ld;
-#pragma unroll
-  for (int u = 0; u < SP_SITES; ++u) {
-    const int xl = threadIdx.x + SP_THREADS * u;
-    if (xl >= nx) break;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      P16 pr[NPC], pi[NPC];
-      make_pieces<BF16, FIXED, NPC>(w[u][c].re, sc, pr);
-      make_pieces<BF16, FIXED, NPC>(w[u][c].im, sc, pi);
-      const long long k = 3LL * xl + c;
-#pragma unroll
-      for (int i = 0; i < NPC; ++i) {
-        base[(2 * i) * ps + k] = pr[i];
-        base[(2 * i + 1) * ps + k] = pi[i];
-      }
-    }
-  }
-}
+};
 
 struct ESrc {  // rows i*np + q, K = (x, a) from K0 (3 V3 < 2^31)
   const float2* v;
@@ -246,12 +191,7 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
   cfg.err = ctx->d_error;
   for (long long K0 = 0; K0 < Ktot; K0 += EL_KC) {
     const int Kc = (int)((Ktot - K0) < EL_KC ? (Ktot - K0) : EL_KC);
-    {
-      Launch Lz(ctx, "split_pairs", s);
-      split_pairs_kernel<BF16, FIXED, NA><<<(unsigned)P2, SP_THREADS, 0, s>>>(
-          vt, w.pairs, V3, K0 / 3, Kc / 3, H, reinterpret_cast<typename tc::Piece<BF16>::T*>(w.W), w.ldk, P2, w.eW);
-    }
-    DISTIL_LAUNCH_CHECK();
+    DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_pairs", WSrc{vt, w.pairs, V3, (int)K0}, P2, P2, Kc, H, w.W, w.ldk, w.eW, s)));
     DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_phase", ESrc{vt, w.tab, mom, V3, (int)K0}, R, R, Kc, H, w.E, w.ldk, w.eE, s)));
     Planes A = planes_of(w.W, Kc, P2, 1, NPLA, w.ldk);
     Planes B = planes_of(w.E, Kc, R, 1, NPLB, w.ldk);
