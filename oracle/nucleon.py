@@ -171,6 +171,17 @@ def source_spin(nu: int) -> dict:
 # ---------------------------------------------------------------------------
 
 
+def eigenvalue_profiles(lam: np.ndarray, sigmas) -> np.ndarray:
+    """Quark distillation profiles as functions of the Laplacian eigenvalues
+    (Sec. 2.1: the profiles "can be a function of the 3D Laplacian
+    eigenvalues"), Gaussian in the eigenvalue:
+        g^(b)_i[t] = exp(-(lam_i[t] / sigma_b)^2).
+    lam: [nv] or [nt][nv]; returns [nb][nv] or [nt][nb][nv]."""
+    lam = np.asarray(lam, dtype=np.float64)
+    sig = np.asarray(sigmas, dtype=np.float64)
+    return np.exp(-(lam[..., None, :] / sig[:, None]) ** 2)
+
+
 def profile_scale(phi_dense: np.ndarray, g: np.ndarray) -> np.ndarray:
     """Phi^(a)_ijk = g_i g_j g_k Phi_ijk (no sum)."""
     return phi_dense * g[:, None, None] * g[None, :, None] * g[None, None, :]

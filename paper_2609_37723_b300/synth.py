@@ -21,7 +21,8 @@ Conventions (all fixed here, used by every consumer):
 * momenta  mom[q] = integer triples n, p = 2*pi*n/L.
 
 Random streams: numpy PCG64 seeded by SeedSequence(2609, spawn_key=(config,
-cfg, t, field)) with field 0 = eigenvectors, 1 = perambulator, 2 = N_v draw.
+cfg, t, field)) with field 0 = eigenvectors, 1 = perambulator, 2 = N_v draw,
+3 = Laplacian eigenvalues.
 """
 from __future__ import annotations
 
@@ -33,7 +34,7 @@ import numpy as np
 from scipy.linalg import solve_triangular
 
 BASE_SEED = 2609
-FIELD_V, FIELD_TAU, FIELD_NV = 0, 1, 2
+FIELD_V, FIELD_TAU, FIELD_NV, FIELD_LAMBDA = 0, 1, 2, 3
 
 
 def rng_for(config: int, cfg: int, t: int, field: int) -> np.random.Generator:
@@ -106,6 +107,16 @@ class Problem:
         rng = rng_for(self.config_id, self.cfg, t, FIELD_TAU)
         n4 = 4 * self.nv
         return (complex_gaussian(rng, (n4, n4)) * math.exp(-self.tau_decay * t)).astype(self.dtype)
+
+    def laplacian_eigenvalues(self, t: int) -> np.ndarray:
+        """Stand-in for the eigenvalues of the N_v lowest modes of the 3D
+        Laplacian at timeslice t (the vectors here are random, so any
+        increasing positive sequence serves): 0.05 (i+1)^(2/3) times a seeded
+        jitter of +-5 %, sorted ascending, float64 [nv]."""
+        rng = rng_for(self.config_id, self.cfg, t, FIELD_LAMBDA)
+        i = np.arange(self.nv, dtype=np.float64)
+        lam = 0.05 * (i + 1.0) ** (2.0 / 3.0) * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, self.nv))
+        return np.sort(lam)
 
     def all_eigvecs(self, ts: Optional[Sequence[int]] = None) -> np.ndarray:
         ts = range(self.nt) if ts is None else ts

@@ -359,3 +359,21 @@ def test_optimal_correlator_is_phase_invariant_and_diagonalises():
     np.testing.assert_allclose(orc.optimal_correlator(C, rot), orc.optimal_correlator(C, ref), rtol=1e-12)
     off = ref[0].conj() @ C[0, :, :, 5] @ ref[0].T
     assert np.abs(off - np.diag(np.diag(off))).max() < 1e-10 * np.abs(np.diag(off)).max()
+
+
+def test_eigenvalue_profiles():
+    """g^(b)_i = exp(-(lam_i / sigma_b)^2): one at lam = 0, 1/e at lam = sigma,
+    decreasing in lam, unchanged when lam and sigma scale together, and per
+    timeslice when lam carries a time axis."""
+    lam = np.array([0.0, 0.1, 0.2, 0.4, 1.0])
+    g = orc.eigenvalue_profiles(lam, [0.2, 1.0])
+    assert g.shape == (2, 5)
+    assert g[0, 0] == 1.0 and g[1, 0] == 1.0
+    assert abs(g[0, 2] - np.exp(-1.0)) < 1e-15 and abs(g[1, 4] - np.exp(-1.0)) < 1e-15
+    assert np.all(np.diff(g, axis=1) < 0)
+    np.testing.assert_allclose(orc.eigenvalue_profiles(3 * lam, [0.6, 3.0]), g, rtol=1e-14)  # ratios differ by an ulp
+    lam_t = np.stack([lam, 2 * lam])
+    gt = orc.eigenvalue_profiles(lam_t, [0.2, 1.0])
+    assert gt.shape == (2, 2, 5)
+    np.testing.assert_array_equal(gt[0], g)
+    np.testing.assert_allclose(gt[1], orc.eigenvalue_profiles(2 * lam, [0.2, 1.0]), rtol=0)
