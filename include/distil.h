@@ -206,6 +206,19 @@ int distil_gevp_range(distil_ctx* ctx, const void* C, int np, int nb, int nt, in
 int distil_optimal(distil_ctx* ctx, const void* C, int np, int nb, int nt, const void* vecs,
                    int td, void* copt, double* meff, distil_stream stream);
 
+/* Quark distillation profiles as functions of the Laplacian eigenvalues
+ * (Sec. 2.1: the profiles "can be a function of the 3D Laplacian
+ * eigenvalues" and of t), Gaussian in the eigenvalue:
+ *   prof[t][b][i] = exp(-(lam[t][i] / sigma[b])^2)
+ *   lam   [nt][nv] f64 device: eigenvalue of distillation vector i at t
+ *   sigma [nb] f64 HOST, each > 0, read during the call
+ *   prof  [nt][nb][nv] f64 device: the per-timeslice profiles
+ *         distil_correlate takes with prof_per_t = 1 (nt = 1: the
+ *         t-independent [nb][nv] form)
+ * Sizes: nt, nv >= 1, 1 <= nb <= 16. */
+int distil_profiles_eigen(distil_ctx* ctx, const double* lam, int nt, int nv, const double* sigma,
+                          int nb, double* prof, distil_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Split-precision complex GEMM (the tensor-core engine on its own)    */
 /* ------------------------------------------------------------------ */
@@ -337,6 +350,23 @@ void distil_plan_destroy(distil_plan* plan);
  * DISTIL_ETIMEOUT with a message when it is nonzero.  reset != 0 clears
  * the word afterwards.  code may be NULL. */
 int distil_device_status(distil_ctx* ctx, int reset, unsigned* code);
+
+/* Limit, in SM clock cycles, of the bounded waits inside the tensor-core
+ * pipelines of ctx (a TMA stage, a free stage, the accumulator); cycles <= 0
+ * restores the default of 2^31 (about a second at 2 GHz).  On expiry a
+ * kernel records the code read by distil_device_status and returns; the
+ * teardown waits for copies and MMAs still in flight keep the default limit.
+ * A short limit makes the next tensor-core call fail on purpose (failure
+ * detection without a device fault).  Host only. */
+int distil_set_wait_limit(distil_ctx* ctx, long long cycles);
+
+/* Scan count values of x (f64, or f32 when is_f32) for NaN or Inf;
+ * synchronises `stream`.  Returns DISTIL_OK with *first_bad = -1 when all
+ * are finite, else DISTIL_EINVAL with *first_bad = the lowest index of a
+ * non-finite value (a complex array is scanned as 2 count reals).
+ * first_bad may be NULL.  For validating inputs before a call. */
+int distil_scan_finite(distil_ctx* ctx, const void* x, long long count, int is_f32,
+                       long long* first_bad, distil_stream stream);
 
 /* 1 if this build implements `mode`, else 0 (no device needed). */
 int distil_mode_supported(int mode);

@@ -26,8 +26,41 @@ int gevp_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, 
                 void* lambda, void* vecs, cudaStream_t s);
 int optimal_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, const void* vecs, int td, void* copt,
                    double* meff, cudaStream_t s);
+int eigen_profiles_launch(distil_ctx* ctx, const double* lam, int nt, int nv, const double* sigma, int nb,
+                          double* prof, cudaStream_t s);
 
 Profiler& profiler(distil_ctx* ctx) { return *ctx->prof; }
+
+// Lowest index of a NaN or Inf among x[0, count) into the 64-bit word *slot
+// (which starts at LLONG_MAX).
+__global__ void scan_finite_kernel(const void* __restrict__ x, long long count, int f32,
+                                   unsigned long long* __restrict__ slot) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool fin = f32 ? isfinite(static_cast<const float*>(x)[i]) : isfinite(static_cast<const double*>(x)[i]);
+    if (!fin) atomicMin(slot, (unsigned long long)i);
+  }
+}
+
+// Synchronous on `s`: *bad = the first non-finite element or -1.  The scan
+// uses the spare 64-bit word of the context's device status buffer.
+int scan_finite_launch(distil_ctx* ctx, const void* x, long long count, bool f32, long long* bad, cudaStream_t s) {
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(ctx->d_error + 2);
+  const unsigned long long init = ~0ull;
+  DISTIL_CUDA(cudaMemcpyAsync(slot, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  if (count > 0) {
+    Launch L(ctx, "scan_finite", s);
+    long long blocks = (count + 255) / 256;
+    if (blocks > 4 * 148 * 8) blocks = 4 * 148 * 8;
+    scan_finite_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, count, f32 ? 1 : 0, slot);
+  }
+  DISTIL_LAUNCH_CHECK();
+  unsigned long long got = 0;
+  DISTIL_CUDA(cudaMemcpyAsync(&got, slot, sizeof(got), cudaMemcpyDeviceToHost, s));
+  DISTIL_CUDA(cudaStreamSynchronize(s));
+  *bad = got == ~0ull ? -1 : (long long)got;
+  return DISTIL_OK;
+}
 
 // Make the context's device current for this call.
 static int enter(distil_ctx* ctx) {
@@ -65,6 +98,7 @@ int distil_create(int device, distil_ctx** out) {
   c->tune[0] = 1;  // step i (K = N_v): persistent, epilogue overlapped (2 measured slower at N_v = 128)
   c->tune[1] = 0;  // step j (K = 4 N_v): one 128 x 128 tile per CTA
   c->tune[2] = 0;  // T contraction (K = 5 N_v, three accumulator pairs): one tile per CTA
+  c->wait_limit = 0;
   if (cudaMalloc(&c->d_error, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMemset(c->d_error, 0, sizeof(unsigned int) * 4) != cudaSuccess) {
     set_error("distil_create: cannot allocate the device error word");
@@ -290,6 +324,41 @@ int distil_device_status(distil_ctx* ctx, int reset, unsigned* code) {
                                  "epilogue waiting for the accumulator", "teardown waiting for copies in flight"};
     set_error("a bounded device wait expired: %s (code %u)", w < 5 ? what[w] : "unknown", w);
     return DISTIL_ETIMEOUT;
+  }
+  return DISTIL_OK;
+}
+
+int distil_profiles_eigen(distil_ctx* ctx, const double* lam, int nt, int nv, const double* sigma, int nb,
+                          double* prof, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(lam && sigma && prof, "distil_profiles_eigen: null pointer");
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && nb >= 1 && nb <= 16, "distil_profiles_eigen: bad sizes");
+  DISTIL_CHECK_ARG(aligned(lam, 8) && aligned(prof, 8), "distil_profiles_eigen: misaligned pointer");
+  for (int b = 0; b < nb; ++b)
+    DISTIL_CHECK_ARG(sigma[b] > 0.0 && sigma[b] < 1e300, "distil_profiles_eigen: sigma[%d] must be positive", b);
+  return eigen_profiles_launch(ctx, lam, nt, nv, sigma, nb, prof, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_set_wait_limit(distil_ctx* ctx, long long cycles) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(ctx != nullptr, "distil_set_wait_limit: null context");
+  ctx->wait_limit = cycles > 0 ? cycles : 0;
+  return DISTIL_OK;
+}
+
+int distil_scan_finite(distil_ctx* ctx, const void* x, long long count, int is_f32, long long* first_bad,
+                       distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(count >= 0 && (x != nullptr || count == 0), "distil_scan_finite: null array");
+  DISTIL_CHECK_ARG(aligned(x, is_f32 ? 4 : 8), "distil_scan_finite: misaligned array");
+  long long bad = -1;
+  DISTIL_TRY(scan_finite_launch(ctx, x, count, is_f32 != 0, &bad, reinterpret_cast<cudaStream_t>(stream)));
+  if (first_bad) *first_bad = bad;
+  if (bad >= 0) {
+    set_error("distil_scan_finite: non-finite value (NaN or Inf) at element %lld", bad);
+    return DISTIL_EINVAL;
   }
   return DISTIL_OK;
 }

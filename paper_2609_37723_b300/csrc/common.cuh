@@ -130,4 +130,7 @@ struct distil_ctx {
   // with two 128 x 64 accumulator sets; set by distil_set_tuning or the
   // plan autotuner
   int tune[3];
+  // limit of the tensor-core pipeline waits in SM clock cycles (0: the
+  // default of about a second); distil_set_wait_limit
+  long long wait_limit;
 };

@@ -287,6 +287,38 @@ int optimal_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, const
   return DISTIL_OK;
 }
 
+// Profiles as Gaussians in the Laplacian eigenvalue: prof[t][b][i] =
+// exp(-(lam[t][i] / sigma_b)^2), FP64 (the paper's profiles "can be a
+// function of the 3D Laplacian eigenvalues", Sec. 2.1).  The N_B <= 16
+// widths travel in the kernel arguments.
+struct ProfileWidths {
+  double sigma[16];
+};
+__global__ void eigen_profiles_kernel(const double* __restrict__ lam, int nt, int nv, ProfileWidths w, int nb,
+                                      double* __restrict__ prof) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)nt * nb * nv;
+  if (e >= total) return;
+  const int i = (int)(e % nv);
+  const long long tb = e / nv;
+  const int b = (int)(tb % nb), t = (int)(tb / nb);
+  const double x = lam[(long long)t * nv + i] / w.sigma[b];
+  prof[e] = exp(-x * x);
+}
+
+int eigen_profiles_launch(distil_ctx* ctx, const double* lam, int nt, int nv, const double* sigma, int nb,
+                          double* prof, cudaStream_t s) {
+  ProfileWidths w{};
+  for (int b = 0; b < nb && b < 16; ++b) w.sigma[b] = sigma[b];
+  const long long total = (long long)nt * nb * nv;
+  {
+    Launch L(ctx, "eigen_profiles", s);
+    eigen_profiles_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(lam, nt, nv, w, nb, prof);
+  }
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
 int gevp_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, int t0, int t_begin, int t_count,
                 void* lambda, void* vecs, cudaStream_t s) {
   int total = np * t_count;

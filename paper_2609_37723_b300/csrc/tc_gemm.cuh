@@ -47,6 +47,7 @@ struct GemmCfg {
   float w1;   // weight of the cross-term accumulator pairs
   int shift;  // D *= 2^(eA + eB - shift)
   unsigned* err;
+  long long wait;  // limit of the pipeline waits in clock cycles (teardown waits keep TC_WAIT_CYCLES)
 };
 
 // Products of the split schemes, by operand planes: 3 x 4 pieces (6
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT) || *(volatile uint32_t*)abort_flag) {
+      if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT, cfg.wait) || *(volatile uint32_t*)abort_flag) {
         *(volatile uint32_t*)abort_flag = 1;
         break;
       }
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *(volatile uint32_t*)abort_flag) {
+      if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT, cfg.wait) || *(volatile uint32_t*)abort_flag) {
         *(volatile uint32_t*)abort_flag = 1;
         break;
       }
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;             // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;   // which half of the NT columns
-    bool ok = mbar_wait(accf, 0, cfg.err, TC_ERR_ACC_WAIT);
+    bool ok = mbar_wait(accf, 0, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
     ok = __all_sync(0xffffffffu, ok && !*(volatile uint32_t*)abort_flag);  // warp-uniform for tcgen05.ld
     tc_fence_after();
     if (ok) {
@@ -333,13 +334,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
   }
   __syncthreads();
-  if (threadIdx.x == 0 && *(volatile uint32_t*)abort_flag) {
-    // drain: wait (bounded) for the last load of every stage, so no copy
-    // lands in shared memory after the CTA has exited
-    const int issued = (int)*(volatile uint32_t*)issued_s;
-    for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
-      if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
+  if (threadIdx.x == 0) {
+    if (*(volatile uint32_t*)abort_flag) {
+      // drain: wait (bounded) for the last load of every stage, so no copy
+      // lands in shared memory after the CTA has exited
+      const int issued = (int)*(volatile uint32_t*)issued_s;
+      for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, cfg.err, TC_ERR_DRAIN)) break;
+      }
     }
+    // every MMA issued has completed before TMEM is freed (the epilogue's
+    // own wait may have given up early)
+    mbar_wait(accf, 0, cfg.err, TC_ERR_DRAIN);
   }
   __syncthreads();
   if (warp == 1) {
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % STAGES);
         const uint32_t ph = (g / STAGES) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT) || *abort_v) {
+        if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT, cfg.wait) || *abort_v) {
           *abort_v = 1;
           break;
         }
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
       const uint32_t buf = it & 1, use = it >> 1;
-      if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT) || *abort_v) {
+      if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait) || *abort_v) {
         *abort_v = 1;
         break;
       }
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % STAGES);
         const uint32_t ph = (g / STAGES) & 1;
-        if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *abort_v) {
+        if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT, cfg.wait) || *abort_v) {
           *abort_v = 1;
           ok = false;
           break;
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
       const uint32_t buf = it & 1, use = it >> 1;
-      bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT);
+      bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
       ok = __all_sync(0xffffffffu, ok && !*abort_v);  // warp-uniform for tcgen05.ld
       if (!ok) {
         if (lane == 0) *abort_v = 1;
@@ -607,7 +613,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
       if (rest != key) {
         // the previous A tile is overwritten only after its last MMA completed
-        if (reloads > 0 && !mbar_wait(afree, (reloads - 1) & 1, cfg.err, TC_ERR_EMPTY_WAIT)) {
+        if (reloads > 0 && !mbar_wait(afree, (reloads - 1) & 1, cfg.err, TC_ERR_EMPTY_WAIT, cfg.wait)) {
           *abort_v = 1;
           break;
         }
@@ -624,7 +630,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % STAGES);
         const uint32_t ph = (g / STAGES) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT) || *abort_v) {
+        if (!mbar_wait(&empty[s], ph ^ 1, cfg.err, TC_ERR_EMPTY_WAIT, cfg.wait) || *abort_v) {
           *abort_v = 1;
           ok = false;
           break;
@@ -645,7 +651,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = t_begin; t < t_end && !*abort_v; ++t) {
       const int rest = t / n_tiles;
       if (rest != key) {
-        if (!mbar_wait(afull, reloads & 1, cfg.err, TC_ERR_FULL_WAIT) || *abort_v) {
+        if (!mbar_wait(afull, reloads & 1, cfg.err, TC_ERR_FULL_WAIT, cfg.wait) || *abort_v) {
           *abort_v = 1;
           break;
         }
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         key = rest;
       }
       const uint32_t buf = it & 1, use = it >> 1;
-      if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT) || *abort_v) {
+      if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait) || *abort_v) {
         *abort_v = 1;
         break;
       }
@@ -663,7 +669,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % STAGES);
         const uint32_t ph = (g / STAGES) & 1;
-        if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT) || *abort_v) {
+        if (!mbar_wait(&full[s], ph, cfg.err, TC_ERR_FULL_WAIT, cfg.wait) || *abort_v) {
           *abort_v = 1;
           ok = false;
           break;
@@ -699,7 +705,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = t_begin; t < t_end; ++t) {
       const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
       const uint32_t buf = it & 1, use = it >> 1;
-      bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT);
+      bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
       ok = __all_sync(0xffffffffu, ok && !*abort_v);
       if (!ok) {
         if (lane == 0) *abort_v = 1;

@@ -38,6 +38,7 @@ template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC = 
 int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg_in,
                 int batch, const Epi& epi, cudaStream_t s) {
   GemmCfg cfg = cfg_in;
+  cfg.wait = (ctx && ctx->wait_limit > 0) ? ctx->wait_limit : TC_WAIT_CYCLES;
   if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
   if (cfg.K <= 0) {
     set_error("%s: K must be positive", name);
@@ -76,6 +77,7 @@ template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC = 
 int launch_gemm_persistent(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B,
                            const GemmCfg& cfg_in, int batch, const Epi& epi, cudaStream_t s) {
   GemmCfg cfg = cfg_in;
+  cfg.wait = (ctx && ctx->wait_limit > 0) ? ctx->wait_limit : TC_WAIT_CYCLES;
   if (cfg.M <= 0 || cfg.N <= 0 || batch <= 0) return DISTIL_OK;
   if (cfg.K <= 0) {
     set_error("%s: K must be positive", name);
@@ -117,6 +119,7 @@ template <int NT, int KC, int NPLA, int NPLB, int NKA, bool BF16, int NACC = 2, 
 int launch_gemm_ares(distil_ctx* ctx, const char* name, const Planes& A, const Planes& B, const GemmCfg& cfg_in,
                      int batch, const Epi& epi, cudaStream_t s) {
   GemmCfg cfg = cfg_in;
+  cfg.wait = (ctx && ctx->wait_limit > 0) ? ctx->wait_limit : TC_WAIT_CYCLES;
   using G = TileGeom<NT, KC, NPLA, NPLB>;
   constexpr size_t room = 232448 - 1024 - 256 - (size_t)NKA * G::A_STAGE;
   constexpr int ST0 = (int)(room / G::B_STAGE);

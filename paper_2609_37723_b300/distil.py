@@ -38,7 +38,8 @@ EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_mode_supported", "distil_profile_enable", "distil_profile_read",
            "distil_device_status", "distil_set_tuning", "distil_get_tuning",
            "distil_plan_workspace", "distil_plan_create", "distil_plan_run", "distil_plan_info",
-           "distil_plan_destroy"]
+           "distil_plan_destroy", "distil_set_wait_limit", "distil_scan_finite",
+           "distil_profiles_eigen"]
 
 _lib = None
 _ctx = {}
@@ -113,6 +114,13 @@ def _declare(L):
     L.distil_optimal.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                  c_void_p]
     L.distil_optimal.restype = c_int
+    L.distil_profiles_eigen.argtypes = [c_void_p, c_void_p, c_int, c_int, P(ctypes.c_double), c_int, c_void_p,
+                                        c_void_p]
+    L.distil_profiles_eigen.restype = c_int
+    L.distil_set_wait_limit.argtypes = [c_void_p, ctypes.c_longlong]
+    L.distil_set_wait_limit.restype = c_int
+    L.distil_scan_finite.argtypes = [c_void_p, c_void_p, ctypes.c_longlong, c_int, P(ctypes.c_longlong), c_void_p]
+    L.distil_scan_finite.restype = c_int
     L.distil_cgemm_workspace.argtypes = [c_int, c_int, c_int, c_int, c_int, P(c_size_t)]
     L.distil_cgemm_workspace.restype = c_int
     L.distil_cgemm.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int,
@@ -341,6 +349,45 @@ def device_status(reset: bool = False, device: int = 0) -> int:
     code = ctypes.c_uint()
     _check(lib().distil_device_status(context(device), int(reset), ctypes.byref(code)))
     return int(code.value)
+
+
+def profiles_eigen(lam, sigmas, stream=None):
+    """Profiles exp(-(lam_i / sigma_b)^2) from Laplacian eigenvalues lam
+    ([nt][nv] or [nv], f64 on the GPU): [nt][nb][nv] (or [nb][nv])."""
+    import torch
+    squeeze = lam.dim() == 1
+    lam2 = lam[None] if squeeze else lam
+    assert lam2.dtype == torch.float64 and lam2.is_cuda and lam2.is_contiguous()
+    nt, nv = int(lam2.shape[0]), int(lam2.shape[1])
+    sig = (ctypes.c_double * len(sigmas))(*[float(x) for x in sigmas])
+    out = torch.empty((nt, len(sigmas), nv), dtype=torch.float64, device=lam.device)
+    _check(lib().distil_profiles_eigen(context(lam.device.index or 0), _ptr(lam2), nt, nv, sig, len(sigmas),
+                                       _ptr(out), _stream(stream)))
+    return out[0] if squeeze else out
+
+
+def set_wait_limit(cycles: int, device: int = 0):
+    """Limit of the tensor-core pipeline waits in clock cycles (<= 0: default)."""
+    _check(lib().distil_set_wait_limit(context(device), int(cycles)))
+
+
+def scan_finite(x, stream=None) -> int:
+    """Index of the first NaN/Inf among the real values of tensor x (complex
+    tensors are scanned as interleaved reals), or -1; raises DistilError
+    (EINVAL) when there is one."""
+    import torch
+    assert x.is_cuda and x.is_contiguous()
+    f32 = x.dtype in (torch.float32, torch.complex64)
+    assert f32 or x.dtype in (torch.float64, torch.complex128)
+    count = x.numel() * (2 if x.is_complex() else 1)
+    bad = ctypes.c_longlong()
+    st = lib().distil_scan_finite(context(x.device.index or 0), _ptr(x), count, int(f32), ctypes.byref(bad),
+                                  _stream(stream))
+    if st != 0 and bad.value < 0:
+        _check(st)
+    if st != 0:
+        raise DistilError(st, lib().distil_last_error().decode())
+    return int(bad.value)
 
 
 def profile_enable(timing: bool = False, device: int = 0):

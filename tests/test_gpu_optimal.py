@@ -159,3 +159,38 @@ def test_per_timeslice_profiles_every_mode(cuda_lib, mode, tol):
         distil.correlate_slice(phi[t].contiguous(), phi[0].contiguous(), tau[t].contiguous(), T(prof_t[t]),
                                T(prof_t[0]), C, t, mode)
     assert max_c_error(C.cpu().numpy(), ref) < tol
+
+
+def test_eigenvalue_profiles_match_oracle(cuda_lib):
+    """Profiles from the Laplacian eigenvalues (Sec. 2.1) on the GPU against
+    the oracle's exp(-(lam/sigma)^2), per timeslice."""
+    from paper_2609_37723_b300 import distil
+    p = synth.config(2)
+    lam = np.stack([p.laplacian_eigenvalues(t) for t in range(4)])
+    sig = [0.1, 0.3, 0.6, 1.2]
+    got = distil.profiles_eigen(T(lam), sig).cpu().numpy()
+    ref = orc.eigenvalue_profiles(lam, sig)
+    assert got.shape == (4, 4, p.nv)
+    assert np.abs(got - ref).max() < 1e-15
+    one = distil.profiles_eigen(T(lam[0]), sig).cpu().numpy()
+    assert np.array_equal(one, got[0])
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("fp16x6", 1e-6)])
+def test_correlator_with_eigenvalue_profiles(cuda_lib, mode, tol):
+    """The chain with per-timeslice eigenvalue profiles made on the GPU:
+    elementals -> C_ab(t) (sink g[t], source g[0]) against the oracle."""
+    from paper_2609_37723_b300 import distil
+    p = synth.small(4, 3, 14, mom=[(0, 0, 0), (1, 0, 1)], sigmas=(0.5,), seed_cfg=41,
+                    dtype=np.complex128 if mode == "fp64" else np.complex64)
+    lam = np.stack([p.laplacian_eigenvalues(t) for t in range(p.nt)])
+    sig = [0.08, 0.15, 0.4]
+    v, tau = p.all_eigvecs(), p.all_perambulators()
+    prof_ref = orc.eigenvalue_profiles(lam, sig)
+    phi_ref = orc.elementals(v, p.L, p.mom)
+    ref = orc.correlator(phi_ref, phi_ref[0], tau, prof_ref, prof_per_t=True)
+    prof = distil.profiles_eigen(T(lam), sig)
+    phi = distil.elementals(T(v), p.L, p.mom, mode)
+    got = distil.correlate(phi, phi[0].contiguous(), T(tau), prof, mode, prof_per_t=True).cpu().numpy()
+    print(f"eigenvalue profiles {mode}: strict per-entry {max_c_error(got, ref):.2e}")
+    assert max_c_error(got, ref) < tol
