@@ -41,6 +41,9 @@ SAMPLES = {
     "L32_Nt64_Nv128": (3, 0, [(t, p) for t in (0, 1, 32, 63) for p in (0, 4)]),
     # one configuration of the uneven ensemble with N_v = 96 (7 momenta)
     "L32_Nt64_cfg3_Nv96": (4, 3, [(t, p) for t in (0, 1, 32, 63) for p in (0, 6)]),
+    # two more members of the ensemble, N_v = 128 and 64, first two timeslices
+    "L32_Nt64_cfg0_Nv128": (4, 0, [(t, p) for t in (0, 1) for p in (0, 6)]),
+    "L32_Nt64_cfg1_Nv64": (4, 1, [(t, p) for t in (0, 1) for p in (0, 6)]),
     # L = 48, N_t = 96, N_v = 256, 9 momenta, 8 profiles: an early slice at
     # p = 0 and the last timeslice at the last momentum
     "L48_Nt96_Nv256": (5, 0, [(1, 0), (95, 8)]),
