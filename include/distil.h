@@ -274,15 +274,18 @@ int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* p
 
 /* Tensor-core kernel variant of each mode-contraction site of the mixed
  * correlator, variants[3] = {step i (K = N_v), step j (K = 4 N_v), the T
- * contraction Z = W T^c of the final sum (K = 5 N_v)}: 0 = one 128 x NT
- * tile per CTA (NT = 128, or 80 / 64 at the sites that keep three
- * accumulator pairs), 1 = persistent CTAs with two accumulator sets
- * (128 x 64, or 128 x 32 with three pairs), 2 (step i only) = persistent
- * with the whole-K A tile resident in shared memory (used when N_v <= 128,
- * else variant 1).  Every variant of a site gives identical results; only
- * the speed differs.  The defaults are {1, 0, 0}.  The library has no
- * counterpart of this in the paper: it is a property of this
- * implementation. */
+ * contraction Z = W T^c of the final sum (K = 5 N_v)}:
+ *   0  one 128 x NT tile per CTA, NT = 128 (or 80 / 64, whichever pads
+ *      less, at the sites that keep three accumulator pairs)
+ *   1  persistent CTAs with two accumulator sets, 128 x 64 tiles (128 x 32
+ *      with three pairs)
+ *   2  step i only: persistent with the whole-K A tile resident in shared
+ *      memory (used when N_v <= 128, else variant 1)
+ *   3  one 128 x 64 tile per CTA
+ *   4  persistent, 128 x 32 tiles
+ * Every variant of a site gives identical results; only the speed differs.
+ * The defaults are {1, 0, 0}.  The library has no counterpart of this in
+ * the paper: it is a property of this implementation. */
 int distil_set_tuning(distil_ctx* ctx, const int* variants);
 int distil_get_tuning(const distil_ctx* ctx, int* variants);
 
@@ -315,7 +318,8 @@ int distil_plan_workspace(const distil_batch_shape* shape, const distil_batch_cf
                           size_t* bytes);
 
 /* Build a plan: optionally autotune (autotune != 0: run the correlator of
- * the first configuration on its first timeslice once per kernel variant,
+ * the first configuration on its first timeslice once per candidate vector
+ * of kernel variants (five, covering every variant of every site),
  * with event timing, and keep the faster variant of every site; this runs
  * eagerly on `stream`, synchronises it and resets the context's kernel
  * statistics), then capture, on `stream`, the whole ensemble (per

@@ -298,7 +298,7 @@ int distil_set_tuning(distil_ctx* ctx, const int* variants) {
   g_err[0] = 0;
   DISTIL_CHECK_ARG(ctx != nullptr && variants != nullptr, "distil_set_tuning: null pointer");
   for (int i = 0; i < 3; ++i)
-    DISTIL_CHECK_ARG(variants[i] == 0 || variants[i] == 1 || (i == 0 && variants[i] == 2),
+    DISTIL_CHECK_ARG(variants[i] >= 0 && variants[i] <= 4 && (i == 0 || variants[i] != 2),
                      "distil_set_tuning: variant %d of site %d", variants[i], i);
   for (int i = 0; i < 3; ++i) ctx->tune[i] = variants[i];
   return DISTIL_OK;

@@ -545,13 +545,17 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
 }
 
 // Mode-contraction GEMM in the kernel variant the context's tuning table
-// names for this site (step i, step j, and the T contraction, which the
-// tuning table and the ABI call the "source" site: it replaced the
-// source-side contraction and has its K = 5 N_v): 0 = one 128 x NT tile per CTA (wide MMAs, no overlap
-// of epilogue and MMAs), 1 = persistent CTAs with two accumulator sets (the
-// epilogue of one tile overlaps the MMAs of the next), 2 = the same with the
-// whole-K A tile resident in shared memory across the column tiles of a
-// batch (K <= 128; else variant 1).  NACC is a property of the site, not of
+// names for this site (step i, step j, and the T contraction with K = 5 N_v,
+// which took the tuning slot of the former source-side contraction):
+//   0  one 128 x NT tile per CTA, NT the widest TMEM allows (128, or 80 /
+//      64 by padding cost with three accumulator pairs); no overlap of
+//      epilogue and MMAs
+//   1  persistent CTAs with two accumulator sets (the epilogue of one tile
+//      overlaps the MMAs of the next), 128 x 64 (128 x 32 with three pairs)
+//   2  step i only: as 1 with the whole-K A tile resident in shared memory
+//      across the column tiles of a batch (K <= 128; else variant 1)
+//   3  one 128 x 64 tile per CTA
+//   4  persistent, 128 x 32 tiles  NACC is a property of the site, not of
 // the variant: step j (K = 4 N_v) and the T contraction (K = 5 N_v)
 // accumulate the 6-product schemes in three pairs (exact cross terms; the
 // second-order terms drift with K otherwise), step i (K = N_v) in two.  All variants of a site
@@ -565,18 +569,22 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& 
   constexpr int NKA = 8;  // resident A covers K <= 128
   constexpr int NTP = NACC == 3 ? 32 : 64;    // persistent: two sets of 2 NACC NT columns
   constexpr int NTW = NACC == 3 ? 80 : 128;   // one-tile: 2 NACC NT columns
+  const int var = ctx->tune[site];
   if constexpr (NACC == 2) {
-    if (ctx->tune[site] == 2 && cfg.K <= NKA * KC && cfg.N > 32)
+    if (var == 2 && cfg.K <= NKA * KC && cfg.N > 32)
       return tc::launch_gemm_ares<64, KC, NPLA, NPLB, NKA, BF16, NACC>(ctx, name, A, B, cfg, batch, epi, s);
+    if (var == 4)  // persistent, narrow tiles
+      return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16, NACC>(
+          ctx, name, A, B, cfg, batch, epi, s);
   }
-  if (ctx->tune[site] >= 1) {
+  if (var == 1 || var == 2 || var == 4) {
     if (cfg.N > 32)
       return tc::launch_gemm_persistent<NTP, KC, NPLA, NPLB, tc::max_stages<NTP, KC, NPLA, NPLB>(), BF16, NACC>(
           ctx, name, A, B, cfg, batch, epi, s);
     return tc::launch_gemm_persistent<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16, NACC>(
         ctx, name, A, B, cfg, batch, epi, s);
   }
-  if (cfg.N > 64) {
+  if (cfg.N > 64 && var == 0) {
     if constexpr (NACC == 3) {
       // 80-wide tiles read A once per 80 columns, 64-wide ones waste no
       // padding when N is a multiple of 64: shared-memory reads per output
@@ -590,6 +598,7 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& 
     return tc::launch_gemm<NTW, KC, NPLA, NPLB, tc::max_stages<NTW, KC, NPLA, NPLB>(), BF16, NACC>(
         ctx, name, A, B, cfg, batch, epi, s);
   }
+  // variant 3, and narrow N: one-tile, 64 (or 32) wide
   if (cfg.N > 32)
     return tc::launch_gemm<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16, NACC>(ctx, name, A, B, cfg,
                                                                                                 batch, epi, s);

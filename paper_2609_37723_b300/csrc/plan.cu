@@ -129,18 +129,19 @@ int distil_plan_create(distil_ctx* ctx, const distil_batch_shape* shape, const d
 
   const bool mixed = shape->mode != DISTIL_FP64 && shape->mode != DISTIL_FP32;
   if (autotune && mixed) {
-    // candidate vectors: every variant of every site appears (variant 2
+    // candidate vectors: every variant of every site appears once (variant 2
     // exists for step i only); each site keeps its fastest
-    static const int cand[3][3] = {{0, 0, 0}, {1, 1, 1}, {2, 1, 1}};
-    double t[3][3];
-    for (int v = 0; v < 3; ++v) {
+    constexpr int NC = 5;
+    static const int cand[NC][3] = {{0, 0, 0}, {1, 1, 1}, {2, 3, 3}, {3, 4, 4}, {4, 0, 0}};
+    double t[NC][3];
+    for (int v = 0; v < NC; ++v) {
       DISTIL_TRY(distil_set_tuning(ctx, cand[v]));
       DISTIL_TRY(time_sites(ctx, shape, cfgs[0], phi, ws, wsb, stream, t[v]));
     }
     int best[3];
     for (int k = 0; k < 3; ++k) {
       int bv = 0;
-      for (int v = 1; v < 3; ++v)
+      for (int v = 1; v < NC; ++v)
         if (t[v][k] < t[bv][k]) bv = v;
       best[k] = cand[bv][k];
     }

@@ -442,18 +442,59 @@ def plan_workspace(L, nt, mom, nb, mode, nvs) -> int:
     return b.value
 
 
+def tuning_cache_key(gpu_name: str, L: int, nt: int, np_: int, nb: int, mode, nvs) -> str:
+    """Key of a tuned plan in the tuning cache: the GPU and the shape the
+    variants were timed on (the autotuner times the first configuration; the
+    largest N_v of the ensemble is part of the key)."""
+    return f"{gpu_name}|L{int(L)}|nt{int(nt)}|np{int(np_)}|nb{int(nb)}|{MODE_NAMES[_mode(mode)]}|nv{max(nvs)}"
+
+
+def load_tuning_cache(path: str) -> dict:
+    """{key: [variants]} from a JSON tuning cache ({} if absent or unreadable)."""
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {k: [int(x) for x in v] for k, v in d.items() if isinstance(v, list) and len(v) == 3}
+    except (OSError, ValueError):
+        return {}
+
+
+def store_tuning(path: str, key: str, variants) -> None:
+    """Add or replace one entry of the JSON tuning cache (written to a
+    temporary file, then renamed over the old one)."""
+    import json
+    d = load_tuning_cache(path)
+    d[key] = [int(x) for x in variants]
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Plan:
     """An ensemble of configurations (shared L, nt, momenta, nb, mode; each
     with its own N_v) captured into one CUDA graph.  cfgs: list of dicts
     with device tensors v, tau, prof (f64 [nb][nv]) and outputs C
-    ([np][nb][nb][nt] c128) and optionally lam ([np][nt][nb] c128)."""
+    ([np][nb][nb][nt] c128) and optionally lam ([np][nt][nb] c128).
+    tuning_cache: path of a JSON file of autotuned kernel variants keyed by
+    GPU name and shape; a hit skips the autotuner, a miss stores its choice."""
 
-    def __init__(self, L, nt, mom, nb, t0, mode, cfgs, autotune=True, stream=None):
+    def __init__(self, L, nt, mom, nb, t0, mode, cfgs, autotune=True, stream=None, tuning_cache=None):
         import torch
         self.cfgs = cfgs
         dev = cfgs[0]["v"].device
         self.device = dev.index or 0
         self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.cache_hit = False
+        key = None
+        if tuning_cache is not None and autotune:
+            key = tuning_cache_key(torch.cuda.get_device_name(dev), L, nt, len(np.asarray(mom).reshape(-1, 3)), nb,
+                                   mode, [int(c["nv"]) for c in cfgs])
+            hit = load_tuning_cache(tuning_cache).get(key)
+            if hit is not None:
+                set_tuning(hit, device=self.device)
+                autotune, self.cache_hit = False, True
         shape, arr, self._mom = _batch(L, nt, mom, nb, t0, mode, cfgs)
         b = ctypes.c_size_t()
         _check(lib().distil_plan_workspace(ctypes.byref(shape), arr, len(cfgs), ctypes.byref(b)))
@@ -464,6 +505,8 @@ class Plan:
                                         _ptr(self.workspace), b.value, ctypes.c_void_p(self.stream.cuda_stream),
                                         ctypes.byref(h)))
         self.handle = h
+        if key is not None and not self.cache_hit:
+            store_tuning(tuning_cache, key, self.info()[0])
 
     def run(self, stream=None):
         s = self.stream if stream is None else stream

@@ -111,3 +111,27 @@ def test_tuning_and_status_argument_checks(L):
     assert L.distil_device_status(None, 0, ctypes.byref(code)) == 1
     assert b"null" in L.distil_last_error()
     assert L.distil_plan_info(None, arr, None) == 1
+
+
+def test_tuning_cache_round_trip(tmp_path):
+    """The plan autotuner's JSON cache: keyed by GPU name and shape (the
+    largest N_v of the ensemble), entries replaced in place, unreadable files
+    read as empty."""
+    path = str(tmp_path / "tune.json")
+    assert distil.load_tuning_cache(path) == {}
+    k1 = distil.tuning_cache_key("NVIDIA B300 SXM6 AC", 32, 64, 7, 6, "fp16x6", [64, 128, 96])
+    k2 = distil.tuning_cache_key("NVIDIA B300 SXM6 AC", 32, 64, 7, 6, "fp16x6", [64, 96])
+    assert k1 != k2 and k1.endswith("|nv128") and "|fp16x6|" in k1
+    assert distil.tuning_cache_key("X", 32, 64, 7, 6, 5, [8]) == distil.tuning_cache_key("X", 32, 64, 7, 6, "fp16x6", [8])
+    distil.store_tuning(path, k1, [1, 0, 0])
+    distil.store_tuning(path, k2, [2, 3, 0])
+    distil.store_tuning(path, k1, [4, 0, 3])
+    d = distil.load_tuning_cache(path)
+    assert d == {k1: [4, 0, 3], k2: [2, 3, 0]}
+    open(path, "w").write("{not json")
+    assert distil.load_tuning_cache(path) == {}
+
+
+def test_tuning_variant_range(L):
+    arr = (ctypes.c_int * 3)(4, 3, 4)
+    assert L.distil_set_tuning(None, arr) == 1          # null context first

@@ -83,7 +83,7 @@ def test_tuning_variants_give_identical_results(cuda_lib):
     saved = distil.get_tuning()
     try:
         outs = []
-        for var in ([0, 0, 0], [1, 1, 1], [1, 0, 1], [2, 0, 1], [2, 1, 0]):
+        for var in ([0, 0, 0], [1, 1, 1], [1, 0, 1], [2, 0, 1], [2, 1, 0], [3, 3, 3], [4, 4, 4], [0, 4, 3]):
             distil.set_tuning(var)
             outs.append(distil.correlate(phi, phi[0], tau, T(p.prof), "fp16x6").cpu().numpy())
     finally:
@@ -105,3 +105,55 @@ def test_plan_fp64_matches_oracle(cuda_lib):
         got = c["C"].cpu().numpy()
         assert max_c_scaled_error(got, ref) < 1e-12
         assert np.array_equal(c["lam"].cpu().numpy(), distil.gevp(c["C"], 2).cpu().numpy())
+
+
+def test_plan_ensemble_members_at_full_size(cuda_lib, tmp_path):
+    """A plan over three members of the uneven ensemble at their full size
+    (L = 32, N_v = 64, 96 and 128, 7 momenta, 6 profiles), on their first two
+    timeslices (the source at t = 0), autotuned, against stored FP64 oracle
+    values, every entry gated at 1e-6; a second plan of the same shape takes
+    its kernel variants from the tuning cache."""
+    import json
+    import os
+    import torch
+    from paper_2609_37723_b300 import distil
+    from parity import c_entry_errors
+    here = os.path.dirname(os.path.abspath(__file__))
+    names = ["L32_Nt64_cfg1_Nv64", "L32_Nt64_cfg3_Nv96", "L32_Nt64_cfg0_Nv128"]
+    golds = []
+    for n in names:
+        path = os.path.join(here, "golden", f"oracle_{n}.json")
+        if not os.path.exists(path):
+            pytest.skip(f"stored oracle values {n} not generated")
+        golds.append(json.load(open(path)))
+    ts = [0, 1]
+    cfgs, probs = [], []
+    for g in golds:
+        p = synth.config(g["workload"], g["cfg"])
+        assert p.nv == g["nv"]
+        v = np.stack([p.eigvecs(t) for t in ts])
+        tau = np.stack([p.perambulator(t) for t in ts])
+        cfgs.append({"nv": p.nv, "v": T(v), "tau": T(tau), "prof": T(p.prof),
+                     "C": torch.zeros((p.np_, p.nb, p.nb, len(ts)), dtype=torch.complex128, device="cuda"),
+                     "lam": torch.zeros((p.np_, len(ts), p.nb), dtype=torch.complex128, device="cuda")})
+        probs.append(p)
+    p0 = probs[0]
+    cache = str(tmp_path / "tuning.json")
+    plan = distil.Plan(p0.L, len(ts), p0.mom, p0.nb, 1, "fp16x6", cfgs, autotune=True, tuning_cache=cache)
+    variants, kernels = plan.info()
+    assert not plan.cache_hit and os.path.exists(cache)
+    plan.run()
+    plan.stream.synchronize()
+    worst = 0.0
+    for g, c in zip(golds, cfgs):
+        got = c["C"].cpu().numpy()
+        for smp in g["samples"]:
+            ref = np.asarray(smp["C"])[..., 0] + 1j * np.asarray(smp["C"])[..., 1]
+            e = c_entry_errors(got[smp["p"], :, :, smp["t"]][None, :, :, None], ref[None, :, :, None]).max()
+            worst = max(worst, float(e))
+    print(f"plan over N_v = 64, 96, 128 (L = 32): {kernels} kernels, variants {variants}, "
+          f"worst strict per-entry {worst:.2e}")
+    assert worst < 1e-6
+    assert distil.device_status() == 0
+    again = distil.Plan(p0.L, len(ts), p0.mom, p0.nb, 1, "fp16x6", cfgs, autotune=True, tuning_cache=cache)
+    assert again.cache_hit and again.info()[0] == variants
