@@ -45,7 +45,7 @@ def test_plan_uneven_ensemble_mixed(cuda_lib, autotune):
     cfgs = device_cfgs(ens)
     plan = distil.Plan(4, 3, MOM, 2, 1, "fp16x6", cfgs, autotune=autotune)
     variants, kernels = plan.info()
-    assert variants[0] in (0, 1, 2) and variants[1] in (0, 1) and variants[2] in (0, 1)
+    assert variants[0] in range(5) and variants[1] in (0, 1, 3, 4) and variants[2] in (0, 1, 3, 4)
     assert kernels > 10 * len(cfgs)
     assert distil.get_tuning() == variants
     plan.run()
@@ -148,8 +148,10 @@ def test_plan_ensemble_members_at_full_size(cuda_lib, tmp_path):
     for g, c in zip(golds, cfgs):
         got = c["C"].cpu().numpy()
         for smp in g["samples"]:
+            if smp["t"] not in ts:
+                continue
             ref = np.asarray(smp["C"])[..., 0] + 1j * np.asarray(smp["C"])[..., 1]
-            e = c_entry_errors(got[smp["p"], :, :, smp["t"]][None, :, :, None], ref[None, :, :, None]).max()
+            e = c_entry_errors(got[smp["p"], :, :, ts.index(smp["t"])][None, :, :, None], ref[None, :, :, None]).max()
             worst = max(worst, float(e))
     print(f"plan over N_v = 64, 96, 128 (L = 32): {kernels} kernels, variants {variants}, "
           f"worst strict per-entry {worst:.2e}")
