@@ -1031,10 +1031,10 @@ def run_reference(args):
     """The reference arm: the FP64 oracle as it stands on the host cores.
     Workloads 1-4: one (t, p = 0) slice of the workload per step (untimed
     warm-up slices first).  Workload 5 (one slice takes many minutes): each
-    step is the bounded sample of cpu_baseline_sampled on the slice
-    (t = 1, p = 0) -- the oracle's elementals of the first 64 modes and its
-    correlator of the first 96 modes for one source profile (cycling
-    through the profiles), scaled to the full slice by N_v^3 and N_B N_v^4.
+    step is a bounded sample of the slice (t = 1, p = 0) -- the oracle's
+    elementals of the first 40 modes and its correlator of the first 96
+    modes for one source profile (cycling through the profiles), scaled to
+    the full slice by N_v^3 and N_B N_v^4 (about 6 s per step on 16 cores).
     entries/s = N_B^2 per slice / mean (scaled) slice time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -1046,7 +1046,7 @@ def run_reference(args):
         p = synth.config(cid, 0)
         if args.nt > 0:
             p = dataclasses.replace(p, nt=min(p.nt, args.nt))
-        m_el, m_co = 64, 96
+        m_el, m_co = 40, 96
         mom0 = p.mom[:1]
         v1 = p.eigvecs(1).astype(np.complex128)
         tau1 = p.perambulator(1).astype(np.complex128)

@@ -71,14 +71,16 @@ __global__ void c64_exp_kernel(const float2* __restrict__ x, long long len, int*
     exps[blockIdx.x] = row_exponent(m);
   }
 }
-// complex128 -> complex double-float, times 2^-e (one exponent per array)
-__global__ void c128_to_cdf_kernel(const double2* __restrict__ x, long long len, const int* __restrict__ exps,
-                                   CDF* __restrict__ out) {
+// complex128 -> complex double-float, times 2^-e: array y = blockIdx.y of
+// `len` values (input stride xs, output stride len) with exponent exps[y]
+__global__ void c128_to_cdf_kernel(const double2* __restrict__ x, long long len, long long xs,
+                                   const int* __restrict__ exps, CDF* __restrict__ out) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= len) return;
-  const double s = ldexp(1.0, -exps[0]);
-  const double2 v = x[e];
-  out[e] = cdf_make(df_from_double(v.x * s), df_from_double(v.y * s));
+  const int y = blockIdx.y;
+  const double s = ldexp(1.0, -exps[y]);
+  const double2 v = x[y * xs + e];
+  out[y * len + e] = cdf_make(df_from_double(v.x * s), df_from_double(v.y * s));
 }
 __global__ void prof_to_df_kernel(const double* __restrict__ g, long long n, DF* __restrict__ out) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -154,29 +156,39 @@ __device__ __forceinline__ CDF phi_at(const CDF* phi, int i, int j, int k, DF w)
   if (x > y) { int t = x; x = y; y = t; neg = !neg; }
   return cdf_scale(phi[triple_rank(x, y, z)], neg ? df_neg(w) : w);
 }
-struct GSrc {  // rows a*n^2 + k*n + j, K = i: g_i g_j g_k Phi_ijk
-  const CDF* phi;
-  const DF* g;
-  int n;
-  __device__ __forceinline__ CDF operator()(long long r, int i) const {
+struct GSrc {  // rows (qb nb + a) n^2 + k n + j, K = i: g_i g_j g_k Phi_ijk of momentum qb of the batch
+  const CDF* phi;  // [qb][T3]
+  const DF* g;     // [nb][n]
+  int n, nb;
+  long long T3;
+  __device__ __forceinline__ void unpack(long long r, const CDF*& ph, const DF*& ga, int& k, int& j) const {
     const long long n2 = (long long)n * n;
-    const int a = (int)(r / n2);
-    const int k = (int)((r % n2) / n), j = (int)(r % n);
-    const DF* ga = g + (long long)a * n;
-    return phi_at(phi, i, j, k, df_mul(df_mul(ga[i], ga[j]), ga[k]));
+    const long long ab = r / n2;
+    const int qb = (int)(ab / nb), a = (int)(ab - (long long)qb * nb);
+    k = (int)((r % n2) / n);
+    j = (int)(r % n);
+    ph = phi + qb * T3;
+    ga = g + (long long)a * n;
+  }
+  __device__ __forceinline__ CDF operator()(long long r, int i) const {
+    const CDF* ph;
+    const DF* ga;
+    int k, j;
+    unpack(r, ph, ga, k, j);
+    return phi_at(ph, i, j, k, df_mul(df_mul(ga[i], ga[j]), ga[k]));
   }
   __device__ __forceinline__ float2 approx(long long r, int i) const {
-    const long long n2 = (long long)n * n;
-    const int a = (int)(r / n2);
-    const int k = (int)((r % n2) / n), j = (int)(r % n);
+    const CDF* ph;
+    const DF* ga;
+    int k, j;
+    unpack(r, ph, ga, k, j);
     if (i == j || j == k || i == k) return make_float2(0.f, 0.f);
     int x = i, y = j, z = k;
     if (x > y) { int t = x; x = y; y = t; }
     if (y > z) { int t = y; y = z; z = t; }
     if (x > y) { int t = x; x = y; y = t; }
-    const DF* ga = g + (long long)a * n;
     const float w = ga[i].hi * ga[j].hi * ga[k].hi;
-    const CDF p = phi[triple_rank(x, y, z)];
+    const CDF p = ph[triple_rank(x, y, z)];
     return make_float2(p.re.hi * w, p.im.hi * w);
   }
 };
@@ -384,14 +396,19 @@ constexpr int DOT_BLOCKS = 1184;  // 8 x 148 SMs
 // sums C_ab as unevaluated double-floats.
 template <int MAXB>
 __global__ void __launch_bounds__(32 * MAXB)
-dot_z_kernel(const CDF* __restrict__ Z, const CDF* __restrict__ phi, const DF* __restrict__ g, int nv, int nb,
-             Cx<double>* __restrict__ part) {
+dot_z_kernel(const CDF* __restrict__ Z, const CDF* __restrict__ phi_all, const DF* __restrict__ g, int nv, int nb,
+             Cx<double>* __restrict__ part_all) {
   __shared__ CDF sphi[32 * MAXB];
   __shared__ DF sgam[MAXB][32 * MAXB];
   const int tile = 32 * nb;
   const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long P2 = comb2(nv);
   const long long work = P2 * nv;
+  // momentum qb of the batch: its Z slabs, source elementals and partial sums
+  const int qb = blockIdx.y;
+  const CDF* phi = phi_all + (long long)qb * comb3(nv);
+  Cx<double>* part = part_all + (long long)qb * gridDim.x * nb * nb;
+  Z += (long long)qb * nb * work;
   float sr[MAXB], cr[MAXB], si[MAXB], ci[MAXB];
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) sr[b] = cr[b] = si[b] = ci[b] = 0.f;
@@ -460,14 +477,17 @@ dot_z_kernel(const CDF* __restrict__ Z, const CDF* __restrict__ phi, const DF* _
 }
 
 // C[a][b] = 2^scale sum over blocks of part[block][a][b]: one block of 256
-// threads per (a, b), each thread summing a fixed stride of the blocks, then
-// a fixed-shape tree, so the order of the additions never changes.
+// threads per (a, b) and momentum qb = blockIdx.y of the batch, each thread
+// summing a fixed stride of the blocks, then a fixed-shape tree, so the
+// order of the additions never changes.  The exponents of momentum qb are
+// esnk[qb], esrc[qb]; its C block starts cstride_q further on.
 __global__ void __launch_bounds__(256)
 dot_reduce_kernel(const Cx<double>* __restrict__ part, int nblocks, int nb, const int* __restrict__ etau,
                   const int* __restrict__ esnk, const int* __restrict__ esrc, Cx<double>* __restrict__ C,
-                  long long cstride_a, long long cstride_b) {
+                  long long cstride_a, long long cstride_b, long long cstride_q) {
   __shared__ double sr[256], si[256];
-  const int ab = blockIdx.x;
+  const int ab = blockIdx.x, qb = blockIdx.y;
+  part += (long long)qb * nblocks * nb * nb;
   double zr = 0.0, zi = 0.0;
   for (int k = threadIdx.x; k < nblocks; k += 256) {
     const Cx<double> p = part[(long long)k * nb * nb + ab];
@@ -485,8 +505,8 @@ dot_reduce_kernel(const Cx<double>* __restrict__ part, int nblocks, int nb, cons
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double scale = ldexp(1.0, 3 * etau[0] + esnk[0] + esrc[0]);
-    Cx<double>& dst = C[(ab / nb) * cstride_a + (ab % nb) * cstride_b];
+    const double scale = ldexp(1.0, 3 * etau[0] + esnk[qb] + esrc[qb]);
+    Cx<double>& dst = C[qb * cstride_q + (ab / nb) * cstride_a + (ab % nb) * cstride_b];
     dst.r = sr[0] * scale;
     dst.i = si[0] * scale;
   }
@@ -504,9 +524,12 @@ struct MixedWs {
   long long ldn, ld4, ld5;
 };
 
-static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, int nb) {
+// Per-timeslice buffers (the tau splits) once; per-momentum buffers for a
+// group of pb momenta processed together.
+static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, int nb, int pb) {
   const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv), T3 = comb3(nv);
   const int npa = 2 * sc.na, npb = 2 * sc.nb;
+  const long long bq = (long long)pb * nb;  // (momentum, profile) slabs of a group
   MixedWs w;
   w.ldn = tc::pad64(n);
   w.ld4 = tc::pad64(4 * n);
@@ -514,23 +537,23 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, 
   w.Aa = ar.take<uint16_t>(12LL * npa * n * w.ldn);
   w.TT = ar.take<uint16_t>((long long)npb * 4 * n * w.ld4);
   w.TcT = ar.take<uint16_t>((long long)npb * n * w.ld5);
-  w.G = ar.take<uint16_t>((long long)nb * npb * n2 * w.ldn);
-  w.U = ar.take<uint16_t>((long long)nb * 3 * npa * n2 * w.ld4);
-  w.W = ar.take<uint16_t>((long long)nb * npa * P2 * w.ld5);
+  w.G = ar.take<uint16_t>(bq * npb * n2 * w.ldn);
+  w.U = ar.take<uint16_t>(bq * 3 * npa * n2 * w.ld4);
+  w.W = ar.take<uint16_t>(bq * npa * P2 * w.ld5);
   w.eAa = ar.take<int>(12 * n);
   w.eTT = ar.take<int>(4 * n);
   w.eTcT = ar.take<int>(n);
-  w.eG = ar.take<int>(nb * n2);
-  w.eU = ar.take<int>(3 * nb * n2);
-  w.eW = ar.take<int>(nb * P2);
+  w.eG = ar.take<int>(bq * n2);
+  w.eU = ar.take<int>(3 * bq * n2);
+  w.eW = ar.take<int>(bq * P2);
   w.nAa = ar.take<float>(12 * n);
-  w.nG = ar.take<float>(nb * n2);
-  w.mG = ar.take<float>(nb * n);
-  w.V = ar.take<CDF>((long long)nb * NPAIR * n3);
-  w.part = ar.take<Cx<double>>((long long)DOT_BLOCKS * nb * nb);
-  w.Z = ar.take<CDF>((long long)nb * P2 * n);
-  w.phs = ar.take<CDF>(T3);
-  w.ph0 = ar.take<CDF>(T3);
+  w.nG = ar.take<float>(bq * n2);
+  w.mG = ar.take<float>(bq * n);
+  w.V = ar.take<CDF>(bq * NPAIR * n3);
+  w.part = ar.take<Cx<double>>((long long)pb * DOT_BLOCKS * nb * nb);
+  w.Z = ar.take<CDF>(bq * P2 * n);
+  w.phs = ar.take<CDF>((long long)pb * T3);
+  w.ph0 = ar.take<CDF>((long long)pb * T3);
   w.g = ar.take<DF>((long long)(nt + 1) * nb * n);
   w.etau = ar.take<int>(nt);
   w.esnk = ar.take<int>((long long)nt * np);
@@ -538,9 +561,24 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, 
   return w;
 }
 
+// Momenta processed together: as many as fit a 32 GiB workspace (all of
+// them for N_v <= 128; one at a time at N_v = 256, whose correlator alone
+// needs ~40 GB).
+constexpr size_t MIXED_GROUP_BUDGET = size_t(32) << 30;
+static int mixed_group(const Scheme& sc, int nt, int nv, int np, int nb) {
+  Arena one, two;
+  carve_mixed(one, sc, nt, nv, np, nb, 1);
+  carve_mixed(two, sc, nt, nv, np, nb, 2);
+  const size_t per = two.used - one.used, base = one.used - per;
+  int pb = 1;
+  while (pb < np && base + (size_t)(pb + 1) * per <= MIXED_GROUP_BUDGET) ++pb;
+  return pb;
+}
+
 size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
+  const Scheme sc = scheme_of(mode);
   Arena ar;
-  carve_mixed(ar, scheme_of(mode), nt, nv, np, nb);
+  carve_mixed(ar, sc, nt, nv, np, nb, mixed_group(sc, nt, nv, np, nb));
   return ar.used + 256;
 }
 
@@ -608,29 +646,43 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& 
 
 static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
 
+// The tau splits of timeslice t (shared by every momentum).
 template <bool BF16, bool FIXED, int NA, int NB>
-static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c128, const double2* ph0_c128,
-                        const float2* tau, const DF* g_snk, const DF* g_src, const int* etau, const int* esnk,
-                        const int* esrc, int nv, int nb, const MixedWs& w, Cx<double>* Cout, long long cs_a,
-                        long long cs_b, cudaStream_t s) {
-  constexpr int NPLA = 2 * NA, NPLB = 2 * NB;
-  const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv), T3 = comb3(nv);
-  using P16 = typename tc::Piece<BF16>::T;
-  {
-    Launch L(ctx, "normalise", s);
-    c128_to_cdf_kernel<<<nblk(T3), 256, 0, s>>>(phs_c128, T3, esnk, w.phs);
-    c128_to_cdf_kernel<<<nblk(T3), 256, 0, s>>>(ph0_c128, T3, esrc, w.ph0);
-  }
-  // ---- split operands (one warp per row, per-row exponents)
+static int split_tau_t(distil_ctx* ctx, const Scheme& sch, const float2* tau, const int* etau, int nv,
+                       const MixedWs& w, cudaStream_t s) {
+  const long long n = nv;
   const int H = sch.H;
   DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_tau", AaSrc{tau, etau, nv}, 12 * n, n, nv, H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
   DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TTSrc{tau, etau, nv}, 4 * n, 4 * n, 4 * nv, H, w.TT, w.ld4, w.eTT, s)));
   DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcTSrc{TcSrc{tau, etau, nv}}, n, n, NSRC * nv, H, w.TcT, w.ld5, w.eTcT, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_sink", GSrc{w.phs, g_snk, nv}, nb * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
+  return DISTIL_OK;
+}
+
+// C_ab(t) of a group of pb momenta q0 .. q0 + pb - 1 at one timeslice, the
+// tau splits of the timeslice already in w: phs_c128 / ph0_c128 point at the
+// group's first sink / source elementals (stride T3), esnk / esrc at its
+// first exponents, Cout at C[q0][0][0][t] (momentum stride cs_q).
+template <bool BF16, bool FIXED, int NA, int NB>
+static int run_group_mixed(distil_ctx* ctx, const Scheme& sch, int pb, const double2* phs_c128,
+                           const double2* ph0_c128, const DF* g_snk, const DF* g_src, const int* etau,
+                           const int* esnk, const int* esrc, int nv, int nb, const MixedWs& w, Cx<double>* Cout,
+                           long long cs_a, long long cs_b, long long cs_q, cudaStream_t s) {
+  constexpr int NPLA = 2 * NA, NPLB = 2 * NB;
+  const long long n = nv, n2 = n * n, n3 = n2 * n, P2 = comb2(nv), T3 = comb3(nv);
+  const long long bq = (long long)pb * nb;  // (momentum, profile) slabs
+  using P16 = typename tc::Piece<BF16>::T;
+  {
+    Launch L(ctx, "normalise", s);
+    c128_to_cdf_kernel<<<dim3(nblk(T3), pb), 256, 0, s>>>(phs_c128, T3, T3, esnk, w.phs);
+    c128_to_cdf_kernel<<<dim3(nblk(T3), pb), 256, 0, s>>>(ph0_c128, T3, T3, esrc, w.ph0);
+  }
+  // ---- sink operand (rows (momentum, profile, k, j), per-row exponents)
+  const int H = sch.H;
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_sink", GSrc{w.phs, g_snk, nv, nb, T3}, bq * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
   {
     Launch L(ctx, "u_exponent", s);
-    g_rowmax_kernel<<<nblk(32LL * nb * n), 256, 0, s>>>(w.nG, nv, nb, w.mG);
-    u_exponent_kernel<<<nblk(3 * nb * n2), 256, 0, s>>>(w.nAa, w.mG, nv, nb, w.eU);
+    g_rowmax_kernel<<<nblk(32LL * bq * n), 256, 0, s>>>(w.nG, nv, (int)bq, w.mG);
+    u_exponent_kernel<<<nblk(3 * bq * n2), 256, 0, s>>>(w.nAa, w.mG, nv, (int)bq, w.eU);
   }
   DISTIL_LAUNCH_CHECK();
 
@@ -638,56 +690,57 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
   fill_products(cfg, sch);
   cfg.err = ctx->d_error;
 
-  // ---- step i: batch (a, a'beta) = nb x 12, output split into U pieces
+  // ---- step i: batch (momentum, a, a'beta) = pb x nb x 12, output split into U pieces
   {
     Planes A = planes_of(w.Aa, n, n, 12, NPLA, w.ldn);
-    Planes B = planes_of(w.G, n, n2, nb, NPLB, w.ldn);
+    Planes B = planes_of(w.G, n, n2, bq, NPLB, w.ldn);
     cfg.M = nv; cfg.N = (int)n2; cfg.K = nv;
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
-    cfg.b = tc::OpMap{12, nb, 1, 0, 0, (int)n2, w.eG};
+    cfg.b = tc::OpMap{12, (int)bq, 1, 0, 0, (int)n2, w.eG};
     EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, nb * 12, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, (int)bq * 12, epi, s)));
   }
-  // ---- step j: per a' (rows b' > a'), batch a; V[a][slot][j'][(i',k)]
+  // ---- step j: per a' (rows b' > a'), batch (momentum, a); V[qa][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
   for (int ap = 0; ap < 3; ++ap) {
-    Planes A = planes_of(w.U, 4 * n, n2, 3LL * nb, NPLA, w.ld4);
+    Planes A = planes_of(w.U, 4 * n, n2, 3 * bq, NPLA, w.ld4);
     Planes B = planes_of(w.TT, 4 * n, 4 * n, 1, NPLB, w.ld4);
     cfg.M = (int)n2; cfg.N = (3 - ap) * nv; cfg.K = 4 * nv;
-    cfg.a = tc::OpMap{1, nb, 3, ap, 0, (int)n2, w.eU};
+    cfg.a = tc::OpMap{1, (int)bq, 3, ap, 0, (int)n2, w.eU};
     cfg.b = tc::OpMap{1, 1, 0, 0, (ap + 1) * nv, 4 * nv, w.eTT};
     EpiStoreCDF epi;
     epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
     epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, nb, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, (int)bq, epi, s)));
   }
-  // ---- W: the source-weighted antisymmetric parts of V, split (rows (a, pair), K = (c, k))
+  // ---- W: the source-weighted antisymmetric parts of V, split (rows (momentum, a, pair), K = (c, k))
   {
     Launch L(ctx, "split_w", s);
     auto* wout = reinterpret_cast<P16*>(w.W);
+    const unsigned rows = (unsigned)(bq * P2);
     if (nv <= 256)
-      split_w_kernel<BF16, FIXED, NA, 1><<<(unsigned)(nb * P2), 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+      split_w_kernel<BF16, FIXED, NA, 1><<<rows, 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
     else if (nv <= 512)
-      split_w_kernel<BF16, FIXED, NA, 2><<<(unsigned)(nb * P2), 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+      split_w_kernel<BF16, FIXED, NA, 2><<<rows, 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
     else
-      split_w_kernel<BF16, FIXED, NA, 4><<<(unsigned)(nb * P2), 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+      split_w_kernel<BF16, FIXED, NA, 4><<<rows, 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
   }
   DISTIL_LAUNCH_CHECK();
-  // ---- T contraction: Z[a][pair][k'] = sum_(c,k) W[a][pair][(c,k)] T^c[k][k'] (K = 5 N_v)
+  // ---- T contraction: Z[qa][pair][k'] = sum_(c,k) W[qa][pair][(c,k)] T^c[k][k'] (K = 5 N_v)
   {
-    Planes A = planes_of(w.W, NSRC * n, P2, nb, NPLA, w.ld5);
+    Planes A = planes_of(w.W, NSRC * n, P2, bq, NPLA, w.ld5);
     Planes B = planes_of(w.TcT, NSRC * n, n, 1, NPLB, w.ld5);
     cfg.M = (int)P2; cfg.N = nv; cfg.K = NSRC * nv;
-    cfg.a = tc::OpMap{1, nb, 1, 0, 0, (int)P2, w.eW};
+    cfg.a = tc::OpMap{1, (int)bq, 1, 0, 0, (int)P2, w.eW};
     cfg.b = tc::OpMap{1, 1, 0, 0, 0, nv, w.eTcT};
     EpiStoreCDF epi;
     epi.out = w.Z;
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
     epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_SOURCE, "tc_gemm_tcontract", A, B, cfg, nb, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_SOURCE, "tc_gemm_tcontract", A, B, cfg, (int)bq, epi, s)));
   }
-  // ---- dot
+  // ---- dot, then the fixed-order reduction into C (momentum on grid y)
   {
     const long long work = P2 * n;
     const long long tile = 32LL * nb;
@@ -695,12 +748,34 @@ static int run_tp_mixed(distil_ctx* ctx, const Scheme& sch, const double2* phs_c
     if (gx > (unsigned)DOT_BLOCKS) gx = DOT_BLOCKS;
     Launch L(ctx, "dot", s);
     if (nb <= 8)
-      dot_z_kernel<8><<<gx, 32 * nb, 0, s>>>(w.Z, w.ph0, g_src, nv, nb, w.part);
+      dot_z_kernel<8><<<dim3(gx, pb), 32 * nb, 0, s>>>(w.Z, w.ph0, g_src, nv, nb, w.part);
     else
-      dot_z_kernel<16><<<gx, 32 * nb, 0, s>>>(w.Z, w.ph0, g_src, nv, nb, w.part);
-    dot_reduce_kernel<<<nb * nb, 256, 0, s>>>(w.part, (int)gx, nb, etau, esnk, esrc, Cout, cs_a, cs_b);
+      dot_z_kernel<16><<<dim3(gx, pb), 32 * nb, 0, s>>>(w.Z, w.ph0, g_src, nv, nb, w.part);
+    dot_reduce_kernel<<<dim3(nb * nb, pb), 256, 0, s>>>(w.part, (int)gx, nb, etau, esnk, esrc, Cout, cs_a, cs_b, cs_q);
   }
   DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
+template <bool BF16, bool FIXED, int NA, int NB>
+static int correlate_mixed_t(distil_ctx* ctx, const Scheme& sch, const void* phi_snk, const void* phi_src,
+                             const void* tau, int nt, int nv, int np, int pb, int prof_per_t, int nb, const DF* g_src,
+                             const MixedWs& w, Cx<double>* Cd, int c_nt, int c_t0, cudaStream_t s) {
+  const long long T3 = comb3(nv), n4 = 4LL * nv;
+  for (int t = 0; t < nt; ++t) {
+    const DF* g_snk = w.g + (prof_per_t ? (long long)t * nb * nv : 0);
+    const float2* ta = (const float2*)tau + (long long)t * n4 * n4;
+    DISTIL_TRY((split_tau_t<BF16, FIXED, NA, NB>(ctx, sch, ta, w.etau + t, nv, w, s)));
+    for (int q0 = 0; q0 < np; q0 += pb) {
+      const int g = np - q0 < pb ? np - q0 : pb;
+      const double2* phs = (const double2*)phi_snk + ((long long)t * np + q0) * T3;
+      const double2* ph0 = (const double2*)phi_src + (long long)q0 * T3;
+      Cx<double>* Cq = Cd + (long long)q0 * nb * nb * c_nt + c_t0 + t;
+      DISTIL_TRY((run_group_mixed<BF16, FIXED, NA, NB>(ctx, sch, g, phs, ph0, g_snk, g_src, w.etau + t,
+                                                      w.esnk + (long long)t * np + q0, w.esrc + q0, nv, nb, w, Cq,
+                                                      (long long)nb * c_nt, c_nt, (long long)nb * nb * c_nt, s)));
+    }
+  }
   return DISTIL_OK;
 }
 
@@ -712,8 +787,9 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   DISTIL_TRY(zero_c_columns(C, (long long)np * nb * nb, c_nt, c_t0, nt, s));
   if (nv < 3) return DISTIL_OK;
   const Scheme sch = scheme_of(mode);
+  const int pb = mixed_group(sch, nt, nv, np, nb);
   Arena ar(ws, ws_bytes);
-  MixedWs w = carve_mixed(ar, sch, nt, nv, np, nb);
+  MixedWs w = carve_mixed(ar, sch, nt, nv, np, nb, pb);
   if (!ar.fits()) {
     set_error("correlate: workspace too small");
     return DISTIL_ENOMEM;
@@ -731,31 +807,17 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   }
   DISTIL_LAUNCH_CHECK();
   Cx<double>* Cd = reinterpret_cast<Cx<double>*>(C);
-  for (int t = 0; t < nt; ++t) {
-    const DF* g_snk = w.g + (prof_per_t ? (long long)t * nb * nv : 0);
-    for (int q = 0; q < np; ++q) {
-      const double2* phs = (const double2*)phi_snk + ((long long)t * np + q) * T3;
-      const double2* ph0 = (const double2*)phi_src + (long long)q * T3;
-      const float2* ta = (const float2*)tau + (long long)t * n4 * n4;
-      Cx<double>* Cq = Cd + (long long)q * nb * nb * c_nt + c_t0 + t;
-      const long long ca = (long long)nb * c_nt, cb = c_nt;
-      const int* et = w.etau + t;
-      const int* es = w.esnk + (long long)t * np + q;
-      const int* e0 = w.esrc + q;
-      int st;
-      if (mode == DISTIL_MIXED_FP16X6)
-        st = run_tp_mixed<false, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb, s);
-      else if (mode == DISTIL_MIXED_BF16X6)
-        st = run_tp_mixed<true, true, 3, 4>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb, s);
-      else if (mode == DISTIL_MIXED_BF16X3)
-        st = run_tp_mixed<true, true, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb, s);
-      else
-        st = run_tp_mixed<false, false, 2, 2>(ctx, sch, phs, ph0, ta, g_snk, g_src, et, es, e0, nv, nb, w, Cq, ca, cb,
-                                              s);
-      if (st != DISTIL_OK) return st;
-    }
-  }
-  return DISTIL_OK;
+  if (mode == DISTIL_MIXED_FP16X6)
+    return correlate_mixed_t<false, true, 3, 4>(ctx, sch, phi_snk, phi_src, tau, nt, nv, np, pb, prof_per_t, nb, g_src,
+                                                w, Cd, c_nt, c_t0, s);
+  if (mode == DISTIL_MIXED_BF16X6)
+    return correlate_mixed_t<true, true, 3, 4>(ctx, sch, phi_snk, phi_src, tau, nt, nv, np, pb, prof_per_t, nb, g_src,
+                                               w, Cd, c_nt, c_t0, s);
+  if (mode == DISTIL_MIXED_BF16X3)
+    return correlate_mixed_t<true, true, 2, 2>(ctx, sch, phi_snk, phi_src, tau, nt, nv, np, pb, prof_per_t, nb, g_src,
+                                               w, Cd, c_nt, c_t0, s);
+  return correlate_mixed_t<false, false, 2, 2>(ctx, sch, phi_snk, phi_src, tau, nt, nv, np, pb, prof_per_t, nb, g_src,
+                                               w, Cd, c_nt, c_t0, s);
 }
 
 }  // namespace distil
