@@ -69,7 +69,7 @@ def _eig_worker(args):
     return len(jobs)
 
 
-def make_inputs(cid: int, cfg: int, workers: int, nt: int = 0, ts=None):
+def make_inputs(cid: int, cfg: int, workers: int, nt: int = 0, ts=None, npm: int = 0):
     """Host inputs of one configuration (numpy, identical bytes to the tests).
     Timeslices are drawn in parallel processes straight into shared memory.
     nt > 0 keeps only the first nt timeslices (a smaller case of the same
@@ -78,6 +78,8 @@ def make_inputs(cid: int, cfg: int, workers: int, nt: int = 0, ts=None):
     p = synth.config(cid, cfg)
     if nt > 0:
         p = dataclasses.replace(p, nt=min(p.nt, nt))
+    if npm > 0:
+        p = dataclasses.replace(p, mom=p.mom[:npm])
     ts = list(range(p.nt)) if ts is None else list(ts)
     shape = (len(ts), p.nv, p.V3, 3)
     dtype = np.dtype(p.dtype)
@@ -293,7 +295,7 @@ def run_ours(args):
     cid = args.workload
     workers = min(32, os.cpu_count() or 1)
     log(f"generating inputs of workload {cid} (cfg {rank}) with {workers} processes")
-    p, v_h, tau_h = make_inputs(cid, rank, workers, args.nt)   # before any CUDA call
+    p, v_h, tau_h = make_inputs(cid, rank, workers, args.nt, npm=args.np)   # before any CUDA call
     log(f"inputs ready: v {v_h.nbytes / 1e9:.2f} GB")
 
     import torch
@@ -1122,6 +1124,8 @@ def main():
                     help="kernel variants of the three contraction sites, e.g. 0,0,0 (default: the library's)")
     ap.add_argument("--nt", type=int, default=0,
                     help="keep only the first NT timeslices (profiling a smaller case; not a bench number)")
+    ap.add_argument("--np", type=int, default=0,
+                    help="workloads 1-3: keep only the first NP momenta (profiling a smaller case; not a bench number)")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(spawn_ranks(args.gpus))

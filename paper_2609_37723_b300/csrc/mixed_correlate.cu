@@ -698,7 +698,9 @@ static int run_group_mixed(distil_ctx* ctx, const Scheme& sch, int pb, const dou
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
     cfg.b = tc::OpMap{12, (int)bq, 1, 0, 0, (int)n2, w.eG};
     EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
+    cfg.order = 1;  // the 2 x 12 tiles that read one G tile run back to back
     DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, (int)bq * 12, epi, s)));
+    cfg.order = 0;
   }
   // ---- step j: per a' (rows b' > a'), batch (momentum, a); V[qa][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};

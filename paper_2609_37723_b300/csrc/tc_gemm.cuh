@@ -48,7 +48,34 @@ struct GemmCfg {
   int shift;  // D *= 2^(eA + eB - shift)
   unsigned* err;
   long long wait;  // limit of the pipeline waits in clock cycles (teardown waits keep TC_WAIT_CYCLES)
+  int order;       // tile order of the persistent and one-tile kernels (tile_at)
 };
+
+// Output tile of linear tile index t.  order 0: n fastest, then m, then
+// batch.  order 1 (B reuse): m fastest, then the b.bdiv consecutive batches
+// that share one B operand, then n, then the rest of the batch -- the tiles
+// that read the same B tile run back to back, so it is fetched from HBM
+// once and served from L2 to the others (step i: 2 x 12 uses per B tile).
+struct TileIdx {
+  int n_tile, m_tile, batch;
+};
+__device__ __forceinline__ TileIdx tile_at(int t, int n_tiles, int m_tiles, const GemmCfg& cfg) {
+  TileIdx r;
+  if (cfg.order == 1) {
+    const int br = cfg.b.bdiv;
+    r.m_tile = t % m_tiles;
+    const int q = t / m_tiles;
+    const int bi = q % br, q2 = q / br;
+    r.n_tile = q2 % n_tiles;
+    r.batch = (q2 / n_tiles) * br + bi;
+  } else {
+    r.n_tile = t % n_tiles;
+    const int rest = t / n_tiles;
+    r.m_tile = rest % m_tiles;
+    r.batch = rest / m_tiles;
+  }
+  return r;
+}
 
 // Products of the split schemes, by operand planes: 3 x 4 pieces (6
 // products, fixed point) or 2 x 2 pieces (3 products).  A product (pa, pb,
@@ -218,14 +245,15 @@ __device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& s
 template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC, class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   GemmCfg cfg, Epi epi) {
+                   GemmCfg cfg, Epi epi, int n_tiles, int m_tiles) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
   static_assert(NT % 16 == 0 && NT >= 32 && NT <= 128 && 2 * NACC * NT <= 512, "N tile / TMEM columns");
   static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
   // a CTA of a launch that already hit a timeout does nothing; the epilogue
   // may declare a tile empty (no output it keeps) before anything is set up
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
-  if (epi.skip_tile(blockIdx.y, blockIdx.x, blockIdx.z)) return;
+  const TileIdx ti = tile_at((int)blockIdx.x, n_tiles, m_tiles, cfg);
+  if (epi.skip_tile(ti.m_tile, ti.n_tile, ti.batch)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t* issued_s = tslot + 2;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y, batch = blockIdx.z;
+  const int n_tile = ti.n_tile, m_tile = ti.m_tile, batch = ti.batch;
   const int nk = (cfg.K + KC - 1) / KC;
   constexpr uint32_t TCOLS = tmem_alloc_cols(2 * NACC * NT);  // D0_re | D0_im | D1_re | D1_im [| D2_re | D2_im]
 
@@ -421,7 +449,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------------------------------------------------------- TMA producer
     uint32_t g = 0;
     for (int t = blockIdx.x; t < total_tiles && !*abort_v; t += gridDim.x) {
-      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      const TileIdx ti = tile_at(t, n_tiles, m_tiles, cfg);
+      const int n_tile = ti.n_tile, m_tile = ti.m_tile, batch = ti.batch;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
       const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
       for (int kb = 0; kb < nk; ++kb, ++g) {
@@ -444,7 +473,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr MmaSchedule<NPLA, NPLB, NACC> S{};
     uint32_t g = 0, it = 0;
     for (int t = blockIdx.x; t < total_tiles && !*abort_v; t += gridDim.x) {
-      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      const TileIdx ti = tile_at(t, n_tiles, m_tiles, cfg);
+      const int n_tile = ti.n_tile, m_tile = ti.m_tile, batch = ti.batch;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
       const uint32_t buf = it & 1, use = it >> 1;
       if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait) || *abort_v) {
@@ -490,7 +520,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int half = (warp - 2) >> 2;   // which half of the NT columns
     uint32_t it = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-      const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
+      const TileIdx ti = tile_at(t, n_tiles, m_tiles, cfg);
+      const int n_tile = ti.n_tile, m_tile = ti.m_tile, batch = ti.batch;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
       const uint32_t buf = it & 1, use = it >> 1;
       bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);

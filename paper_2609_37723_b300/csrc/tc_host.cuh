@@ -59,14 +59,15 @@ int launch_gemm(distil_ctx* ctx, const char* name, const Planes& A, const Planes
     DISTIL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  dim3 grid((unsigned)((cfg.N + NT - 1) / NT), (unsigned)((cfg.M + 127) / 128), (unsigned)batch);
-  if (grid.y > 65535 || grid.z > 65535) {
-    set_error("%s: grid too large", name);
+  const long long n_tiles = (cfg.N + NT - 1) / NT, m_tiles = (cfg.M + 127) / 128;
+  const long long total = n_tiles * m_tiles * batch;
+  if (total > 0x7fffffffLL) {
+    set_error("%s: too many tiles", name);
     return DISTIL_EINVAL;
   }
   {
     Launch L(ctx, name, s);
-    kern<<<grid, TC_THREADS, smem, s>>>(ma, mb, cfg, epi);
+    kern<<<(unsigned)total, TC_THREADS, smem, s>>>(ma, mb, cfg, epi, (int)n_tiles, (int)m_tiles);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
