@@ -973,11 +973,15 @@ def kernel_cmacs(name, p):
     return table.get(name)
 
 
-# DRAM bytes (read + write) per launch from ncu's dram__bytes_* counters of
-# each kernel family on the workload L32_Nt64_Nv128 (first two timeslices:
-# the per-launch units are those of the full size), for the kernels as they
-# stand; empty when they changed after the last capture.
-TRAFFIC_L32_NV128 = {}
+# DRAM bytes (read + write) per launch of a kernel family, from one ncu
+# capture of the kernels as they stand: (workload, mode, kernel) -> bytes.
+# The L48_Nt96_Nv256 elementals launch is too large to capture with
+# --set full; its figure is the L32_Nv128 one-timeslice capture (537 MB read,
+# 3 MB written, profiles/tc_gemm_L32_Nv128_one_timeslice.md) scaled by the
+# operand units of a launch, (pairs + (i, p) rows) x K chunk: x 4.23.
+TRAFFIC = {
+    ("L48_Nt96_Nv256", "fp16x6", "tc_gemm_elementals"): 540.0e6 * (32640 + 2304) / (8128 + 128),
+}
 
 
 def roofline(dom, kstats, p, mode, pk, steps):
@@ -1002,7 +1006,7 @@ def roofline(dom, kstats, p, mode, pk, steps):
         bound = "tensor"
         note = (f"achieved = 8 x {prod} split products x complex MACs / event time: tensor flops the "
                 f"kernel must issue; peak = measured bf16 sustained (fp16 runs at the same rate)")
-    traffic = TRAFFIC_L32_NV128.get(dom) if (p.L, p.nv, p.np_, p.nb) == (32, 128, 5, 6) and mode == "fp16x6" else None
+    traffic = TRAFFIC.get((p.name, mode, dom))
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if peak else None, "traffic": traffic, "per_unit": what,
             "launches": launches, "ms": ms, "note": note}

@@ -24,6 +24,8 @@
 //   T contr. Z[a][pair][k']         = sum_(c,k) W TcT
 //   dot      C_ab = sum_(pair,k') Z^a gamma^b conj(Phi_src~), with
 //            gamma^b = g^b_i' g^b_j' g^b_k' the only b-dependence
+#include <algorithm>
+
 #include "correlate.cuh"
 #include "df.cuh"
 #include "mixed.cuh"
@@ -41,35 +43,31 @@ __device__ __forceinline__ int dbl_exp_bound(double x) {
   const int ex = (int)((b >> 52) & 0x7ff);
   return ex == 0 ? -1022 : ex - 1022;  // |x| < 2^(ex - 1023 + 1)
 }
-// exps[i] for array i of `count` arrays of `len` complex128 values
-__global__ void c128_exp_kernel(const double2* __restrict__ x, long long len, int* __restrict__ exps) {
-  const double2* a = x + (long long)blockIdx.x * len;
-  int m = -1022;
-  for (long long e = threadIdx.x; e < len; e += blockDim.x) {
-    m = max(m, max(dbl_exp_bound(a[e].x), dbl_exp_bound(a[e].y)));
-  }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ int red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
-    exps[blockIdx.x] = max(m, red[0]);
-  }
+// exps[i] >= every element's exponent bound of complex128 array i (of
+// `count` arrays of `len` values): array i = blockIdx.y, spread over
+// gridDim.x blocks that combine with atomicMax into exps[i], which must
+// start below -1022 (exp_init_kernel)
+__global__ void exp_init_kernel(int* __restrict__ exps, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) exps[i] = -2147483647;
 }
-// exps[i] with max |x| < 2^exps[i] for complex64 array i
+__global__ void c128_exp_kernel(const double2* __restrict__ x, long long len, int* __restrict__ exps) {
+  const double2* a = x + (long long)blockIdx.y * len;
+  int m = -1022;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
+    m = max(m, max(dbl_exp_bound(a[e].x), dbl_exp_bound(a[e].y)));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&exps[blockIdx.y], m);
+}
+// exps[i] with max |x| < 2^exps[i] for complex64 array i = blockIdx.y
+// (same scheme; the row exponent of the block maximum is monotone in it)
 __global__ void c64_exp_kernel(const float2* __restrict__ x, long long len, int* __restrict__ exps) {
-  const float2* a = x + (long long)blockIdx.x * len;
+  const float2* a = x + (long long)blockIdx.y * len;
   float m = 0.f;
-  for (long long e = threadIdx.x; e < len; e += blockDim.x) m = fmaxf(m, fmaxf(fabsf(a[e].x), fabsf(a[e].y)));
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(a[e].x), fabsf(a[e].y)));
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ float red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
-    exps[blockIdx.x] = row_exponent(m);
-  }
+  if ((threadIdx.x & 31) == 0) atomicMax(&exps[blockIdx.y], row_exponent(m));
 }
 // complex128 -> complex double-float, times 2^-e: array y = blockIdx.y of
 // `len` values (input stride xs, output stride len) with exponent exps[y]
@@ -801,9 +799,15 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
   DF* g_src = w.g + (long long)nt * nb * nv;  // the source profiles follow the sink blocks
   {
     Launch L(ctx, "normalise", s);
-    c64_exp_kernel<<<nt, 256, 0, s>>>((const float2*)tau, n4 * n4, w.etau);
-    c128_exp_kernel<<<nt * np, 256, 0, s>>>((const double2*)phi_snk, T3, w.esnk);
-    c128_exp_kernel<<<np, 256, 0, s>>>((const double2*)phi_src, T3, w.esrc);
+    // exponents: every array spread over up to 64 blocks
+    const unsigned bt = (unsigned)std::min<long long>(64, (n4 * n4 + 8191) / 8192);
+    const unsigned bp = (unsigned)std::min<long long>(64, (T3 + 8191) / 8192);
+    exp_init_kernel<<<nblk(nt), 256, 0, s>>>(w.etau, nt);
+    exp_init_kernel<<<nblk((long long)nt * np), 256, 0, s>>>(w.esnk, nt * np);
+    exp_init_kernel<<<nblk(np), 256, 0, s>>>(w.esrc, np);
+    c64_exp_kernel<<<dim3(bt, nt), 256, 0, s>>>((const float2*)tau, n4 * n4, w.etau);
+    c128_exp_kernel<<<dim3(bp, nt * np), 256, 0, s>>>((const double2*)phi_snk, T3, w.esnk);
+    c128_exp_kernel<<<dim3(bp, np), 256, 0, s>>>((const double2*)phi_src, T3, w.esrc);
     prof_to_df_kernel<<<nblk(nprof), 256, 0, s>>>(prof_snk, nprof, w.g);
     prof_to_df_kernel<<<nblk((long long)nb * nv), 256, 0, s>>>(prof_src, (long long)nb * nv, g_src);
   }
