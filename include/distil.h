@@ -283,8 +283,11 @@ int distil_correlate_noalloc(distil_ctx* ctx, const void* phi_snk, const void* p
  *      memory (used when N_v <= 128, else variant 1)
  *   3  one 128 x 64 tile per CTA
  *   4  persistent, 128 x 32 tiles
+ *   5  persistent with one accumulator set of the variant-0 tile (the MMAs
+ *      of a tile wait for the previous tile's epilogue while the operand
+ *      copies of the next tile already run)
  * Every variant of a site gives identical results; only the speed differs.
- * The defaults are {1, 0, 0}.  The library has no counterpart of this in
+ * The defaults are {5, 5, 5}.  The library has no counterpart of this in
  * the paper: it is a property of this implementation. */
 int distil_set_tuning(distil_ctx* ctx, const int* variants);
 int distil_get_tuning(const distil_ctx* ctx, int* variants);
@@ -319,7 +322,7 @@ int distil_plan_workspace(const distil_batch_shape* shape, const distil_batch_cf
 
 /* Build a plan: optionally autotune (autotune != 0: run the correlator of
  * the first configuration on its first timeslice once per candidate vector
- * of kernel variants (five, covering every variant of every site),
+ * of kernel variants (six, covering every variant of every site),
  * with event timing, and keep the faster variant of every site; this runs
  * eagerly on `stream`, synchronises it and resets the context's kernel
  * statistics), then capture, on `stream`, the whole ensemble (per
@@ -348,15 +351,15 @@ void distil_plan_destroy(distil_plan* plan);
  * bounded wait that expired (a tensor-core pipeline stage that never
  * arrived); once set, later tensor-core launches of ctx return at once and
  * leave their outputs unwritten.  This call synchronises the device, stores
- * the code in *code (0 = no expired wait; 1 = MMA waiting for a TMA stage,
- * 2 = TMA producer waiting for a free stage, 3 = epilogue waiting for the
+ * the code in *code (0 = no expired wait; 1 = MMA waiting for a copied stage,
+ * 2 = copy producer waiting for a free stage, 3 = epilogue waiting for the
  * accumulator, 4 = teardown waiting for copies in flight) and returns
  * DISTIL_ETIMEOUT with a message when it is nonzero.  reset != 0 clears
  * the word afterwards.  code may be NULL. */
 int distil_device_status(distil_ctx* ctx, int reset, unsigned* code);
 
 /* Limit, in SM clock cycles, of the bounded waits inside the tensor-core
- * pipelines of ctx (a TMA stage, a free stage, the accumulator); cycles <= 0
+ * pipelines of ctx (a copied stage, a free stage, the accumulator); cycles <= 0
  * restores the default of 2^31 (about a second at 2 GHz).  On expiry a
  * kernel records the code read by distil_device_status and returns; the
  * teardown waits for copies and MMAs still in flight keep the default limit.

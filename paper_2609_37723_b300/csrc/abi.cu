@@ -95,9 +95,12 @@ int distil_create(int device, distil_ctx** out) {
   c->cc_minor = prop.minor;
   c->d_error = nullptr;
   c->prof = new Profiler();
-  c->tune[0] = 1;  // step i (K = N_v): persistent, epilogue overlapped (2 measured slower at N_v = 128)
-  c->tune[1] = 0;  // step j (K = 4 N_v): one 128 x 128 tile per CTA
-  c->tune[2] = 0;  // T contraction (K = 5 N_v, three accumulator pairs): one tile per CTA
+  // every site: persistent CTAs with one accumulator set of the widest tile
+  // (128 wide at step i, 80 / 64 with three pairs), the copies of the next
+  // tile running during the epilogue (measured fastest at N_v = 256)
+  c->tune[0] = 5;  // step i (K = N_v)
+  c->tune[1] = 5;  // step j (K = 4 N_v)
+  c->tune[2] = 5;  // T contraction (K = 5 N_v)
   c->wait_limit = 0;
   if (cudaMalloc(&c->d_error, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMemset(c->d_error, 0, sizeof(unsigned int) * 4) != cudaSuccess) {
@@ -298,7 +301,7 @@ int distil_set_tuning(distil_ctx* ctx, const int* variants) {
   g_err[0] = 0;
   DISTIL_CHECK_ARG(ctx != nullptr && variants != nullptr, "distil_set_tuning: null pointer");
   for (int i = 0; i < 3; ++i)
-    DISTIL_CHECK_ARG(variants[i] >= 0 && variants[i] <= 4 && (i == 0 || variants[i] != 2),
+    DISTIL_CHECK_ARG(variants[i] >= 0 && variants[i] <= 5 && (i == 0 || variants[i] != 2),
                      "distil_set_tuning: variant %d of site %d", variants[i], i);
   for (int i = 0; i < 3; ++i) ctx->tune[i] = variants[i];
   return DISTIL_OK;
@@ -320,7 +323,7 @@ int distil_device_status(distil_ctx* ctx, int reset, unsigned* code) {
   if (code) *code = w;
   if (reset) DISTIL_CUDA(cudaMemset(ctx->d_error, 0, sizeof(unsigned)));
   if (w) {
-    static const char* what[] = {"", "MMA waiting for a TMA stage", "TMA producer waiting for a free stage",
+    static const char* what[] = {"", "MMA waiting for a copied stage", "copy producer waiting for a free stage",
                                  "epilogue waiting for the accumulator", "teardown waiting for copies in flight"};
     set_error("a bounded device wait expired: %s (code %u)", w < 5 ? what[w] : "unknown", w);
     return DISTIL_ETIMEOUT;

@@ -144,21 +144,40 @@ __device__ __forceinline__ void make_pieces(DF x, Pow2 s, typename tc::Piece<BF1
   }
 }
 
+// Pieces of element v at K index k of row rr of coordinate c into the 2 NPC
+// planes of img (plane 2 i + re/im holds piece i).  Lanes with consecutive k
+// fill whole 32-byte rows of a K block together.
+template <bool BF16, bool FIXED, int NPC>
+__device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long c, long long rr, int k, const CDF& v,
+                                             Pow2 sc) {
+  using P16 = typename tc::Piece<BF16>::T;
+  P16 pr[NPC], pi[NPC];
+  make_pieces<BF16, FIXED, NPC>(v.re, sc, pr);
+  make_pieces<BF16, FIXED, NPC>(v.im, sc, pi);
+  P16* out = reinterpret_cast<P16*>(img.base) + img.index(c, 0, rr, k);
+  const long long ps = img.rows_pad * 16;  // plane stride in elements
+#pragma unroll
+  for (int i = 0; i < NPC; ++i) {
+    out[(2 * i) * ps] = pr[i];
+    out[(2 * i + 1) * ps] = pi[i];
+  }
+}
+
 // Split rows of a complex operand into 2*NPC planes with a per-row exponent.
-// Global row r = coord * rows_per + rr goes to
-//   out[coord][plane][rr][k]  (plane stride rows_per*ld, coord stride 2*NPC*rows_per*ld)
-// and exps[r]; optionally the row's 2-norm (with a small safety margin)
+// Global row r = coord * img.rows + rr goes to plane image img (tc_gemm.cuh:
+// PlaneImg; plane 2 i + re/im holds piece i) at coordinate coord, row rr,
+// and exps[r]; the K elements of the last K block past img.K are stored as
+// zeros.  Optionally the row's 2-norm (with a small safety margin) goes
 // into norms[r].  One warp per row: pass 1 finds max |re|, |im| over the
 // row, pass 2 writes the pieces.  Src::operator()(r, k) returns the element
 // as a complex double-float, Src::approx(r, k) an FP32 estimate of it.
 template <bool BF16, bool FIXED, int NPC, class Src>
-__global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, long long rows_per, int K, int H,
-                                                         typename tc::Piece<BF16>::T* __restrict__ out, long long ld,
+__global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, tc::PlaneImg img, int H,
                                                          int* __restrict__ exps, float* __restrict__ norms) {
-  using P16 = typename tc::Piece<BF16>::T;
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= nrows) return;
+  const int K = img.K, Kp = img.kblocks * 16;
   float m = 0.f, ss = 0.f;
   for (int k = lane; k < K; k += 32) {
     const float2 v = src.approx(r, k);  // FP32 estimate: enough for the exponent and the norm
@@ -176,35 +195,22 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
     if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
   }
   const Pow2 sc = pow2_pair(H - e);
-  const long long coord = r / rows_per, rr = r % rows_per;
-  const long long ps = rows_per * ld;
-  P16* base = out + coord * (2 * NPC) * ps + rr * ld;
-  for (int k = lane; k < K; k += 32) {
-    const CDF v = src(r, k);
-    P16 pr[NPC], pi[NPC];
-    make_pieces<BF16, FIXED, NPC>(v.re, sc, pr);
-    make_pieces<BF16, FIXED, NPC>(v.im, sc, pi);
-#pragma unroll
-    for (int i = 0; i < NPC; ++i) {
-      base[(2 * i) * ps + k] = pr[i];
-      base[(2 * i + 1) * ps + k] = pi[i];
-    }
-  }
+  const long long coord = r / img.rows, rr = r % img.rows;
+  for (int k = lane; k < Kp; k += 32)
+    store_pieces<BF16, FIXED, NPC>(img, coord, rr, k, k < K ? src(r, k) : cdf_zero(), sc);
 }
 
 // Long rows (K <= 512 PER): one block of 512 threads per row, each thread
 // holding PER elements in registers, so every element is formed once and
 // the exponent comes from the exact maximum.
 template <bool BF16, bool FIXED, int NPC, int PER, class Src>
-__global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, long long rows_per, int K, int H,
-                                                                typename tc::Piece<BF16>::T* __restrict__ out,
-                                                                long long ld, int* __restrict__ exps,
-                                                                float* __restrict__ norms) {
-  using P16 = typename tc::Piece<BF16>::T;
+__global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::PlaneImg img, int H,
+                                                                int* __restrict__ exps, float* __restrict__ norms) {
   __shared__ float red_m[16], red_s[16];
   __shared__ int sh_e;
   const long long r = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int K = img.K, Kp = img.kblocks * 16;
   CDF v[PER];
   float m = 0.f, ss = 0.f;
 #pragma unroll
@@ -228,57 +234,73 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, long lo
   }
   __syncthreads();
   const Pow2 sc = pow2_pair(H - sh_e);
-  const long long coord = r / rows_per, rr = r % rows_per;
-  const long long ps = rows_per * ld;
-  P16* base = out + coord * (2 * NPC) * ps + rr * ld;
+  const long long coord = r / img.rows, rr = r % img.rows;
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int k = threadIdx.x + 512 * u;
-    if (k >= K) break;
-    P16 pr[NPC], pi[NPC];
-    make_pieces<BF16, FIXED, NPC>(v[u].re, sc, pr);
-    make_pieces<BF16, FIXED, NPC>(v[u].im, sc, pi);
-#pragma unroll
-    for (int i = 0; i < NPC; ++i) {
-      base[(2 * i) * ps + k] = pr[i];
-      base[(2 * i + 1) * ps + k] = pi[i];
-    }
+    if (k >= Kp) break;
+    store_pieces<BF16, FIXED, NPC>(img, coord, rr, k, v[u], sc);
   }
 }
 
-// Planes descriptor matching split_rows_kernel's layout.
-inline tc::Planes planes_of(void* base, long long K, long long rows_per, long long ncoord, int npl, long long ld) {
-  return tc::Planes{base, K, rows_per, npl, ncoord, ld, rows_per * ld, (long long)npl * rows_per * ld};
+// Zero the elements past K in the last K block of every row of a plane
+// image whose writer leaves them (the step-i epilogue writes K = 4 N_v
+// elements only): one thread per (coordinate, plane, row).
+static __global__ void img_zero_kpad_kernel(tc::PlaneImg img) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long rows = (long long)img.coords * img.planes * img.rows;
+  if (t >= rows) return;
+  const long long c = t / ((long long)img.planes * img.rows);
+  const int p = (int)((t / img.rows) % img.planes);
+  const long long r = t % img.rows;
+  uint16_t* out = reinterpret_cast<uint16_t*>(img.base);
+  for (int k = img.K; k < img.kblocks * 16; ++k) out[img.index(c, p, r, k)] = 0;
 }
 
 template <bool BF16, bool FIXED, int NPC, class Src>
-inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long long nrows, long long rows_per, int K,
-                      int H, void* out, long long ld, int* exps, cudaStream_t s, float* norms = nullptr) {
+inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long long nrows, const tc::PlaneImg& img,
+                      int H, int* exps, cudaStream_t s, float* norms = nullptr) {
   if (nrows <= 0) return DISTIL_OK;
+  if (img.planes != 2 * NPC || nrows > (long long)img.coords * img.rows || img.kblocks * 16 < img.K) {
+    set_error("%s: rows or planes outside the plane image", name);
+    return DISTIL_EINVAL;
+  }
+  const int K = img.K;
   const long long threads = nrows * 32;
   Launch L(ctx, name, s);
-  auto* o16 = reinterpret_cast<typename tc::Piece<BF16>::T*>(out);
   if (K > 2048 && K <= 4096)
-    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src><<<(unsigned)nrows, 512, 0, s>>>(src, rows_per, K, H, o16, ld, exps, norms);
+    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
   else if (K > 1024 && K <= 2048)
-    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src><<<(unsigned)nrows, 512, 0, s>>>(src, rows_per, K, H, o16, ld, exps, norms);
+    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
   else
-    split_rows_kernel<BF16, FIXED, NPC, Src><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        src, nrows, rows_per, K, H, reinterpret_cast<typename tc::Piece<BF16>::T*>(out), ld, exps, norms);
+    split_rows_kernel<BF16, FIXED, NPC, Src><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, nrows, img, H,
+                                                                                                exps, norms);
+  DISTIL_LAUNCH_CHECK();
+  return DISTIL_OK;
+}
+
+inline int img_zero_kpad(distil_ctx* ctx, const tc::PlaneImg& img, cudaStream_t s) {
+  if (img.kblocks * 16 == img.K) return DISTIL_OK;
+  const long long rows = (long long)img.coords * img.planes * img.rows;
+  Launch L(ctx, "img_zero_kpad", s);
+  img_zero_kpad_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(img);
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
 }
 
 // --------------------------------------------------------------- epilogues
 // Column map shared by the epilogues: colmap(c) = (c / cdiv) * cs1 +
-// (c % cdiv) * sc, or c * sc when cdiv == 0.
+// (c % cdiv) * sc, or c * sc when cdiv == 0; with cdiv, columns whose
+// c % cdiv >= cvalid are padding and are not stored.
 struct ColMap {
   long long sc;
   int cdiv;
   long long cs1;
+  int cvalid;
   __device__ __forceinline__ long long operator()(int c) const {
     return cdiv ? (long long)(c / cdiv) * cs1 + (long long)(c % cdiv) * sc : (long long)c * sc;
   }
+  __device__ __forceinline__ bool keep(int c) const { return !cdiv || (c % cdiv) < cvalid; }
 };
 
 // The GEMM hands the epilogue each value as an unevaluated FP32 pair
@@ -296,11 +318,25 @@ struct EpiStoreCDF : tc::EpiStateless {
   __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     CDF* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
+    if (!cm.cdiv && cm.sc == 1 && col0 + 16 <= N && !(reinterpret_cast<uintptr_t>(base + col0) & 31)) {
+      // 16 contiguous outputs of this row: two per 32-byte store
+      CDF* d = base + col0;
+#pragma unroll
+      for (int e = 0; e < 16; e += 2) {
+        const DF r0 = two_sum(re0[e], re1[e]), i0 = two_sum(im0[e], im1[e]);
+        const DF r1 = two_sum(re0[e + 1], re1[e + 1]), i1 = two_sum(im0[e + 1], im1[e + 1]);
+        const uint32_t w[8] = {__float_as_uint(r0.hi), __float_as_uint(r0.lo), __float_as_uint(i0.hi),
+                               __float_as_uint(i0.lo), __float_as_uint(r1.hi), __float_as_uint(r1.lo),
+                               __float_as_uint(i1.hi), __float_as_uint(i1.lo)};
+        tc::st_global_32B(d + e, w);
+      }
+      return;
+    }
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int c = col0 + e;
       if (c >= N) break;
-      base[cm(c)] = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
+      if (cm.keep(c)) base[cm(c)] = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
     }
   }
 };

@@ -13,6 +13,7 @@
 // Per (t, p):
 //   split    Aa  rows (a'beta, i')  K i        from Gamma_beta tau[(alpha(beta) i)][(a' i')]
 //            tauT rows (b' j')      K (beta j) from tau[(beta j)][(b' j')]
+//                                              (b' blocks of N_v rounded up to 8 rows)
 //            TcT rows k'            K (c, k)   from the five source blocks T^c[k][k']
 //            G   rows (a, (k,j))    K i        from g g g Phi_snk
 //   step i   U[a][a'][(i',k)][(beta,j)] = sum_i Aa G, split by the epilogue
@@ -33,7 +34,7 @@
 
 namespace distil {
 
-using tc::Planes;
+using tc::PlaneImg;
 
 // ------------------------------------------------------------------ setup
 // binary exponent e with |x| < 2^e for the largest |component| of a complex128
@@ -105,18 +106,19 @@ struct AaSrc {  // rows (a'*4 + beta)*n + i', K = i
     return make_float2(v.re.hi, v.im.hi);
   }
 };
-struct TTSrc {  // rows (b'j'), K = (beta j): tau^T
+struct TTSrc {  // rows b' nvp + j' (blocks of nvp >= n rows, the rows past n zero), K = (beta j): tau^T
   const float2* tau;
   const int* etau;
-  int n;
-  __device__ __forceinline__ CDF operator()(long long r, int k) const {
-    return cdf_of(tau[(long long)k * 4 * n + r], tc::pow2f(-etau[0]));
-  }
-  __device__ __forceinline__ float2 approx(long long r, int k) const {
-    const float2 x = tau[(long long)k * 4 * n + r];
+  int n, nvp;
+  __device__ __forceinline__ float2 at(long long r, int k) const {
+    const int bp = (int)(r / nvp), jp = (int)(r % nvp);
+    if (jp >= n) return make_float2(0.f, 0.f);
+    const float2 x = tau[(long long)k * 4 * n + (long long)bp * n + jp];
     const float s = tc::pow2f(-etau[0]);
     return make_float2(x.x * s, x.y * s);
   }
+  __device__ __forceinline__ CDF operator()(long long r, int k) const { return cdf_of(at(r, k), 1.f); }
+  __device__ __forceinline__ float2 approx(long long r, int k) const { return at(r, k); }
 };
 struct TcSrc {  // rows c*n + k, K = k': T^c[k][k']
   const float2* tau;
@@ -218,49 +220,58 @@ __global__ void u_exponent_kernel(const float* __restrict__ nAa, const float* __
 }
 
 // Step i epilogue: split U straight from the accumulator pair into the
-// A-operand pieces of step j, U[(a,a')][plane][(i',k)][(beta,j)].
+// A-operand pieces of step j: plane image U, coordinate (a, a'), row (i', k),
+// K index (beta, j).
 template <bool BF16, bool FIXED, int NPC>
 struct EpiSplitU : tc::EpiStateless {
-  typename tc::Piece<BF16>::T* out;
+  PlaneImg out;
   const int* eU;
   int n, H;
-  long long ld4;
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
   __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     using P16 = typename tc::Piece<BF16>::T;
     const long long n2 = (long long)n * n;
     const int aa = batch >> 2, beta = batch & 3;  // aa = a*3 + a'
-    const long long ps = n2 * ld4;
-    auto* base = out + (long long)aa * (2 * NPC) * ps;
+    P16* o = reinterpret_cast<P16*>(out.base);
     if ((n & 15) == 0 && col0 + 16 <= (int)n2) {
-      // the 16 columns share k and run over 16 consecutive j: assemble each
-      // plane's 16 pieces in registers and write them as two 16-byte stores
+      // the 16 columns share k and run over 16 consecutive j: one 32-byte
+      // row of a K block of the image per plane, assembled in registers
+      // (its two 16-byte halves in the row's swizzled order) and written
+      // with one 32-byte store
       const int k = col0 / n, j0 = col0 % n;
       const long long ur = (long long)row * n + k;
       const Pow2 sc = pow2_pair(H - eU[(long long)aa * n2 + ur]);
-      P16* d = base + ur * ld4 + (long long)beta * n + j0;
+      const int sw = (int)(ur >> 2) & 1;  // halves swapped in this row
+      uint32_t w[2 * NPC][8];
 #pragma unroll
-      for (int h = 0; h < 16; h += 8) {  // 8 columns at a time: one 16-byte store per plane
-        uint32_t w[2 * NPC][4];
+      for (int e = 0; e < 16; e += 2) {
+        P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
+        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr0);
+        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi0);
+        make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), sc, pr1);
+        make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), sc, pi1);
 #pragma unroll
-        for (int e = h; e < h + 8; e += 2) {
-          P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
-          make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr0);
-          make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi0);
-          make_pieces<BF16, FIXED, NPC>(two_sum(re0[e + 1], re1[e + 1]), sc, pr1);
-          make_pieces<BF16, FIXED, NPC>(two_sum(im0[e + 1], im1[e + 1]), sc, pi1);
-#pragma unroll
-          for (int q = 0; q < NPC; ++q) {
-            w[2 * q][(e - h) / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pr0[q]) |
-                                    ((uint32_t)reinterpret_cast<const uint16_t&>(pr1[q]) << 16);
-            w[2 * q + 1][(e - h) / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pi0[q]) |
-                                        ((uint32_t)reinterpret_cast<const uint16_t&>(pi1[q]) << 16);
-          }
+        for (int q = 0; q < NPC; ++q) {
+          w[2 * q][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pr0[q]) |
+                            ((uint32_t)reinterpret_cast<const uint16_t&>(pr1[q]) << 16);
+          w[2 * q + 1][e / 2] = (uint32_t)reinterpret_cast<const uint16_t&>(pi0[q]) |
+                                ((uint32_t)reinterpret_cast<const uint16_t&>(pi1[q]) << 16);
         }
+      }
+      // the row's first element: index of K element beta n + j0 with the
+      // half-swap undone (j0 is a multiple of 16)
+      P16* d = o + ((out.block(aa, (beta * n + j0) >> 4, 0) + ur) << 4);
+      const long long ps = out.rows_pad * 16;
 #pragma unroll
-        for (int pl = 0; pl < 2 * NPC; ++pl)
-          *reinterpret_cast<uint4*>(d + pl * ps + h) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+      for (int pl = 0; pl < 2 * NPC; ++pl) {
+        uint32_t v[8];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          v[x] = sw ? w[pl][4 + x] : w[pl][x];
+          v[4 + x] = sw ? w[pl][x] : w[pl][4 + x];
+        }
+        tc::st_global_32B(d + pl * ps, v);
       }
       return;
     }
@@ -274,7 +285,8 @@ struct EpiSplitU : tc::EpiStateless {
       typename tc::Piece<BF16>::T pr[NPC], pi[NPC];
       make_pieces<BF16, FIXED, NPC>(two_sum(re0[e], re1[e]), sc, pr);
       make_pieces<BF16, FIXED, NPC>(two_sum(im0[e], im1[e]), sc, pi);
-      auto* d = base + ur * ld4 + (long long)beta * n + j;
+      P16* d = o + out.index(aa, 0, ur, beta * n + j);
+      const long long ps = out.rows_pad * 16;
 #pragma unroll
       for (int q = 0; q < NPC; ++q) {
         d[(2 * q) * ps] = pr[q];
@@ -303,11 +315,11 @@ __device__ __forceinline__ CDF ldg_cdf(const CDF* p) {  // p is 16-byte aligned
 // that meet source matrix c (correlate.cuh: coefficients -3, -2 on matrix 0,
 // +-1 on the others), split into NPC fixed-point pieces with one exponent
 // per row (a, pair).  One block per row, thread tid takes k = tid + 256 u.
-//   out[a][plane][pair][c n + k]  (plane stride P2 ld, a stride NPL P2 ld)
+// Plane image out: coordinate a, row pair, K index c n + k (the elements
+// past 5 n in the last K block stored as zeros).
 template <bool BF16, bool FIXED, int NPC, int PER>
 __global__ void __launch_bounds__(256) split_w_kernel(const CDF* __restrict__ V, int nv, long long P2, int H,
-                                                      typename tc::Piece<BF16>::T* __restrict__ out, long long ld,
-                                                      int* __restrict__ exps) {
+                                                      PlaneImg out, int* __restrict__ exps) {
   using P16 = typename tc::Piece<BF16>::T;
   __shared__ float red[8];
   __shared__ int sh_e;
@@ -358,8 +370,8 @@ __global__ void __launch_bounds__(256) split_w_kernel(const CDF* __restrict__ V,
   }
   __syncthreads();
   const Pow2 sc = pow2_pair(H - sh_e);
-  const long long ps = P2 * ld;
-  P16* base = out + (long long)a * (2 * NPC) * ps + pair * ld;
+  P16* o = reinterpret_cast<P16*>(out.base);
+  const long long ps = out.rows_pad * 16;  // plane stride in elements
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int k = threadIdx.x + 256 * u;
@@ -369,13 +381,18 @@ __global__ void __launch_bounds__(256) split_w_kernel(const CDF* __restrict__ V,
       P16 pr[NPC], pi[NPC];
       make_pieces<BF16, FIXED, NPC>(w[u][c].re, sc, pr);
       make_pieces<BF16, FIXED, NPC>(w[u][c].im, sc, pi);
-      const long long kk = (long long)c * nv + k;
+      P16* d = o + out.index(a, 0, pair, c * nv + k);
 #pragma unroll
       for (int q = 0; q < NPC; ++q) {
-        base[(2 * q) * ps + kk] = pr[q];
-        base[(2 * q + 1) * ps + kk] = pi[q];
+        d[(2 * q) * ps] = pr[q];
+        d[(2 * q + 1) * ps] = pi[q];
       }
     }
+  }
+  // zeros past K = NSRC n in the last K block
+  for (int kk = NSRC * nv + (int)threadIdx.x; kk < out.kblocks * 16; kk += 256) {
+#pragma unroll
+    for (int q = 0; q < 2 * NPC; ++q) o[out.index(a, q, pair, kk)] = tc::Piece<BF16>::from(0.f);
   }
 }
 
@@ -512,14 +529,14 @@ dot_reduce_kernel(const Cx<double>* __restrict__ part, int nblocks, int nb, cons
 
 // ------------------------------------------------------------------ workspace
 struct MixedWs {
-  void *Aa, *TT, *TcT, *G, *U, *W;
+  PlaneImg Aa, TT, TcT, G, U, W;  // operand plane images
   int *eAa, *eTT, *eTcT, *eG, *eU, *eW;
   float *nAa, *nG, *mG;
   CDF *V, *Z, *phs, *ph0;
   Cx<double>* part;
   DF* g;
   int *etau, *esnk, *esrc;
-  long long ldn, ld4, ld5;
+  int nvp;  // rows of each b' block of TT: N_v rounded up to 8
 };
 
 // Per-timeslice buffers (the tau splits) once; per-momentum buffers for a
@@ -529,17 +546,19 @@ static MixedWs carve_mixed(Arena& ar, const Scheme& sc, int nt, int nv, int np, 
   const int npa = 2 * sc.na, npb = 2 * sc.nb;
   const long long bq = (long long)pb * nb;  // (momentum, profile) slabs of a group
   MixedWs w;
-  w.ldn = tc::pad64(n);
-  w.ld4 = tc::pad64(4 * n);
-  w.ld5 = tc::pad64((long long)NSRC * n);
-  w.Aa = ar.take<uint16_t>(12LL * npa * n * w.ldn);
-  w.TT = ar.take<uint16_t>((long long)npb * 4 * n * w.ld4);
-  w.TcT = ar.take<uint16_t>((long long)npb * n * w.ld5);
-  w.G = ar.take<uint16_t>(bq * npb * n2 * w.ldn);
-  w.U = ar.take<uint16_t>(bq * 3 * npa * n2 * w.ld4);
-  w.W = ar.take<uint16_t>(bq * npa * P2 * w.ld5);
+  w.nvp = (nv + 7) / 8 * 8;
+  const long long n5 = (long long)NSRC * n, r4 = 4LL * w.nvp;
+  auto img = [&ar](long long K, long long rows, long long coords, int planes) {
+    return tc::plane_img(ar.take<uint16_t>(tc::plane_img_elems(K, rows, coords, planes)), K, rows, coords, planes);
+  };
+  w.Aa = img(n, n, 12, npa);
+  w.TT = img(4 * n, r4, 1, npb);
+  w.TcT = img(n5, n, 1, npb);
+  w.G = img(n, n2, bq, npb);
+  w.U = img(4 * n, n2, 3 * bq, npa);
+  w.W = img(n5, P2, bq, npa);
   w.eAa = ar.take<int>(12 * n);
-  w.eTT = ar.take<int>(4 * n);
+  w.eTT = ar.take<int>(r4);
   w.eTcT = ar.take<int>(n);
   w.eG = ar.take<int>(bq * n2);
   w.eU = ar.take<int>(3 * bq * n2);
@@ -591,21 +610,35 @@ size_t correlate_mixed_workspace(int mode, int nt, int nv, int np, int nb) {
 //   2  step i only: as 1 with the whole-K A tile resident in shared memory
 //      across the column tiles of a batch (K <= 128; else variant 1)
 //   3  one 128 x 64 tile per CTA
-//   4  persistent, 128 x 32 tiles  NACC is a property of the site, not of
-// the variant: step j (K = 4 N_v) and the T contraction (K = 5 N_v)
+//   4  persistent, 128 x 32 tiles
+//   5  persistent with one accumulator set of the widest tile (128, or 80 /
+//      64 with three pairs): the MMAs of a tile wait for the previous
+//      epilogue, the copy ring fills meanwhile
+// NACC is a property of the site, not of the variant: step j (K = 4 N_v) and the T contraction (K = 5 N_v)
 // accumulate the 6-product schemes in three pairs (exact cross terms; the
 // second-order terms drift with K otherwise), step i (K = N_v) in two.  All variants of a site
 // accumulate every element over K in the same order into the same pairs, so
 // they give identical results.
 enum GemmSite { SITE_STEP_I = 0, SITE_STEP_J = 1, SITE_SOURCE = 2 };
 template <bool BF16, int NPLA, int NPLB, int NACC, class Epi>
-static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const Planes& A, const Planes& B,
+static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const PlaneImg& A, const PlaneImg& B,
                 const tc::GemmCfg& cfg, int batch, const Epi& epi, cudaStream_t s) {
   constexpr int KC = 16;
   constexpr int NKA = 8;  // resident A covers K <= 128
   constexpr int NTP = NACC == 3 ? 32 : 64;    // persistent: two sets of 2 NACC NT columns
   constexpr int NTW = NACC == 3 ? 80 : 128;   // one-tile: 2 NACC NT columns
   const int var = ctx->tune[site];
+  if (var == 5 && cfg.N > 64) {
+    if constexpr (NACC == 3) {
+      const double c80 = ((cfg.N + 79) / 80) * 80 * (1.0 / 80 + 1.0 / 128);
+      const double c64 = ((cfg.N + 63) / 64) * 64 * (1.0 / 64 + 1.0 / 128);
+      if (c64 < c80)
+        return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16, NACC, 1>(
+            ctx, name, A, B, cfg, batch, epi, s);
+    }
+    return tc::launch_gemm_persistent<NTW, KC, NPLA, NPLB, tc::max_stages<NTW, KC, NPLA, NPLB>(), BF16, NACC, 1>(
+        ctx, name, A, B, cfg, batch, epi, s);
+  }
   if constexpr (NACC == 2) {
     if (var == 2 && cfg.K <= NKA * KC && cfg.N > 32)
       return tc::launch_gemm_ares<64, KC, NPLA, NPLB, NKA, BF16, NACC>(ctx, name, A, B, cfg, batch, epi, s);
@@ -650,9 +683,9 @@ static int split_tau_t(distil_ctx* ctx, const Scheme& sch, const float2* tau, co
                        const MixedWs& w, cudaStream_t s) {
   const long long n = nv;
   const int H = sch.H;
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_tau", AaSrc{tau, etau, nv}, 12 * n, n, nv, H, w.Aa, w.ldn, w.eAa, s, w.nAa)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TTSrc{tau, etau, nv}, 4 * n, 4 * n, 4 * nv, H, w.TT, w.ld4, w.eTT, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcTSrc{TcSrc{tau, etau, nv}}, n, n, NSRC * nv, H, w.TcT, w.ld5, w.eTcT, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_tau", AaSrc{tau, etau, nv}, 12 * n, w.Aa, H, w.eAa, s, w.nAa)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TTSrc{tau, etau, nv, w.nvp}, 4LL * w.nvp, w.TT, H, w.eTT, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcTSrc{TcSrc{tau, etau, nv}}, n, w.TcT, H, w.eTcT, s)));
   return DISTIL_OK;
 }
 
@@ -676,7 +709,7 @@ static int run_group_mixed(distil_ctx* ctx, const Scheme& sch, int pb, const dou
   }
   // ---- sink operand (rows (momentum, profile, k, j), per-row exponents)
   const int H = sch.H;
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_sink", GSrc{w.phs, g_snk, nv, nb, T3}, bq * n2, n2, nv, H, w.G, w.ldn, w.eG, s, w.nG)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_sink", GSrc{w.phs, g_snk, nv, nb, T3}, bq * n2, w.G, H, w.eG, s, w.nG)));
   {
     Launch L(ctx, "u_exponent", s);
     g_rowmax_kernel<<<nblk(32LL * bq * n), 256, 0, s>>>(w.nG, nv, (int)bq, w.mG);
@@ -690,55 +723,50 @@ static int run_group_mixed(distil_ctx* ctx, const Scheme& sch, int pb, const dou
 
   // ---- step i: batch (momentum, a, a'beta) = pb x nb x 12, output split into U pieces
   {
-    Planes A = planes_of(w.Aa, n, n, 12, NPLA, w.ldn);
-    Planes B = planes_of(w.G, n, n2, bq, NPLB, w.ldn);
     cfg.M = nv; cfg.N = (int)n2; cfg.K = nv;
     cfg.a = tc::OpMap{1, 12, 1, 0, 0, nv, w.eAa};
     cfg.b = tc::OpMap{12, (int)bq, 1, 0, 0, (int)n2, w.eG};
-    EpiSplitU<BF16, FIXED, NA> epi{{}, (P16*)w.U, w.eU, nv, H, w.ld4};
+    EpiSplitU<BF16, FIXED, NA> epi{{}, w.U, w.eU, nv, H};
     cfg.order = 1;  // the 2 x 12 tiles that read one G tile run back to back
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", A, B, cfg, (int)bq * 12, epi, s)));
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_I, "tc_gemm_step_i", w.Aa, w.G, cfg, (int)bq * 12, epi, s)));
     cfg.order = 0;
   }
   // ---- step j: per a' (rows b' > a'), batch (momentum, a); V[qa][slot][j'][(i',k)]
   const int slotbase[3] = {0, 3, 5};
   for (int ap = 0; ap < 3; ++ap) {
-    Planes A = planes_of(w.U, 4 * n, n2, 3 * bq, NPLA, w.ld4);
-    Planes B = planes_of(w.TT, 4 * n, 4 * n, 1, NPLB, w.ld4);
-    cfg.M = (int)n2; cfg.N = (3 - ap) * nv; cfg.K = 4 * nv;
+    // columns (b', j') over the b' blocks of nvp rows; j' >= N_v is padding
+    const int nvp = w.nvp;
+    cfg.M = (int)n2; cfg.N = (3 - ap) * nvp; cfg.K = 4 * nv;
     cfg.a = tc::OpMap{1, (int)bq, 3, ap, 0, (int)n2, w.eU};
-    cfg.b = tc::OpMap{1, 1, 0, 0, (ap + 1) * nv, 4 * nv, w.eTT};
+    cfg.b = tc::OpMap{1, 1, 0, 0, (ap + 1) * nvp, 4 * nvp, w.eTT};
     EpiStoreCDF epi;
     epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
-    epi.sr = 1; epi.cm = ColMap{n2, 0, 0}; epi.N = (3 - ap) * nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", A, B, cfg, (int)bq, epi, s)));
+    epi.sr = 1; epi.cm = ColMap{n2, nvp, n3, nv}; epi.N = (3 - ap) * nvp;
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", w.U, w.TT, cfg, (int)bq, epi, s)));
   }
   // ---- W: the source-weighted antisymmetric parts of V, split (rows (momentum, a, pair), K = (c, k))
   {
     Launch L(ctx, "split_w", s);
-    auto* wout = reinterpret_cast<P16*>(w.W);
     const unsigned rows = (unsigned)(bq * P2);
     if (nv <= 256)
-      split_w_kernel<BF16, FIXED, NA, 1><<<rows, 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+      split_w_kernel<BF16, FIXED, NA, 1><<<rows, 256, 0, s>>>(w.V, nv, P2, H, w.W, w.eW);
     else if (nv <= 512)
-      split_w_kernel<BF16, FIXED, NA, 2><<<rows, 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+      split_w_kernel<BF16, FIXED, NA, 2><<<rows, 256, 0, s>>>(w.V, nv, P2, H, w.W, w.eW);
     else
-      split_w_kernel<BF16, FIXED, NA, 4><<<rows, 256, 0, s>>>(w.V, nv, P2, H, wout, w.ld5, w.eW);
+      split_w_kernel<BF16, FIXED, NA, 4><<<rows, 256, 0, s>>>(w.V, nv, P2, H, w.W, w.eW);
   }
   DISTIL_LAUNCH_CHECK();
   // ---- T contraction: Z[qa][pair][k'] = sum_(c,k) W[qa][pair][(c,k)] T^c[k][k'] (K = 5 N_v)
   {
-    Planes A = planes_of(w.W, NSRC * n, P2, bq, NPLA, w.ld5);
-    Planes B = planes_of(w.TcT, NSRC * n, n, 1, NPLB, w.ld5);
     cfg.M = (int)P2; cfg.N = nv; cfg.K = NSRC * nv;
     cfg.a = tc::OpMap{1, (int)bq, 1, 0, 0, (int)P2, w.eW};
     cfg.b = tc::OpMap{1, 1, 0, 0, 0, nv, w.eTcT};
     EpiStoreCDF epi;
     epi.out = w.Z;
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
-    epi.sr = n; epi.cm = ColMap{1, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_SOURCE, "tc_gemm_tcontract", A, B, cfg, (int)bq, epi, s)));
+    epi.sr = n; epi.cm = ColMap{1, 0, 0, 0}; epi.N = nv;
+    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_SOURCE, "tc_gemm_tcontract", w.W, w.TcT, cfg, (int)bq, epi, s)));
   }
   // ---- dot, then the fixed-order reduction into C (momentum on grid y)
   {
@@ -812,6 +840,7 @@ int correlate_mixed(distil_ctx* ctx, int mode, const void* phi_snk, const void* 
     prof_to_df_kernel<<<nblk((long long)nb * nv), 256, 0, s>>>(prof_src, (long long)nb * nv, g_src);
   }
   DISTIL_LAUNCH_CHECK();
+  DISTIL_TRY(img_zero_kpad(ctx, w.U, s));  // the step-i epilogue writes K = 4 N_v elements only
   Cx<double>* Cd = reinterpret_cast<Cx<double>*>(C);
   if (mode == DISTIL_MIXED_FP16X6)
     return correlate_mixed_t<false, true, 3, 4>(ctx, sch, phi_snk, phi_src, tau, nt, nv, np, pb, prof_per_t, nb, g_src,

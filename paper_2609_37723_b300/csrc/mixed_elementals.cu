@@ -11,7 +11,8 @@
 // split into 16-bit pieces with per-(row, chunk) exponents; the tensor
 // cores accumulate the chunk in TMEM (the leading fixed-point slice
 // exactly), and the epilogue adds the chunk into a double-float accumulator
-// Phi_acc[pair][(i,q)].  Tiles whose every i is >= every j are skipped.  A
+// Phi_acc[(i,q)][pair] (pairs contiguous, so the 32 rows of an epilogue
+// warp read and write 512 contiguous bytes).  Tiles whose every i is >= every j are skipped.  A
 // final pass packs i<j<k into Phi[t][q][rank] as complex128.
 #include <math.h>
 
@@ -22,12 +23,13 @@
 
 namespace distil {
 
-using tc::Planes;
+using tc::PlaneImg;
 
-// K values per accumulation chunk: whole sites (a multiple of 3) and of the
-// 64-value plane padding, so a chunk holds sites [K0/3, (K0 + EL_KC)/3).
+// K values per accumulation chunk: whole sites (a multiple of 3) and whole
+// 16-value K blocks of the plane images, so a chunk holds sites
+// [K0/3, (K0 + EL_KC)/3).
 constexpr int EL_KC = 4032;
-static_assert(EL_KC % 3 == 0 && EL_KC % 64 == 0, "chunks of whole sites, 64-aligned");
+static_assert(EL_KC % 3 == 0 && EL_KC % 16 == 0, "chunks of whole sites and K blocks");
 
 // pairs in j-major order: q -> (j, k), first index j, then k = j+1..n-1
 __host__ __device__ __forceinline__ long long jmajor_first(long long j, long long n) { return j * (2 * n - j - 1) / 2; }
@@ -105,7 +107,7 @@ struct ESrc {  // rows i*np + q, K = (x, a) from K0 (3 V3 < 2^31)
   }
 };
 
-// Phi_acc[q][r] (+)= D for the pair rows q and (i, q') columns r; the first
+// Phi_acc[r][q] (+)= D for the pair rows q and (i, q') columns r; the first
 // chunk stores.  Tiles with min i >= max j hold no kept output.
 struct EpiPhiAcc : tc::EpiStateless {
   CDF* acc;
@@ -121,52 +123,62 @@ struct EpiPhiAcc : tc::EpiStateless {
   }
   __device__ __forceinline__ void operator()(State&, int, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
-    CDF* dst = acc + (long long)row * N + col0;
+    CDF* dst = acc + (long long)col0 * P2 + row;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       if (col0 + e >= N) break;
       CDF v = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
-      if (!first) v = cdf_add(v, dst[e]);
-      dst[e] = v;
+      if (!first) v = cdf_add(v, dst[e * P2]);
+      dst[e * P2] = v;
     }
   }
 };
 
-// Phi[q][rank(i,j,k)] = Phi_acc[pair(j,k)][i*np + q]  (complex128)
-__global__ void pack_phi_kernel(const CDF* __restrict__ acc, int n, int np, double2* __restrict__ phi) {
-  const long long T3 = comb3(n);
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= T3 * np) return;
-  const int q = (int)(e / T3);
-  const long long r = e % T3;
-  // unrank r -> (i, j, k): k from C(k,3) <= r, then (i, j) from r - C(k,3) = C(j,2) + i
-  int k = (int)cbrtf(6.f * (float)r) + 1;
-  while (k > 2 && comb3(k) > r) --k;
-  while (comb3(k + 1) <= r) ++k;
-  int j, i;
-  pair_unrank(r - comb3(k), i, j);
-  const long long qp = jmajor_first(j, n) + (k - j - 1);
-  const CDF v = acc[qp * (long long)(n * np) + (long long)i * np + q];
-  phi[e] = make_double2(df_to_double(v.re), df_to_double(v.im));
+// Phi[q][rank(i,j,k)] = Phi_acc[i*np + q][pair(j,k)]  (complex128), i < j,
+// through 32 x 32 tiles of (i, pair) in shared memory: the accumulator is
+// read along the pairs and Phi written along i (consecutive ranks).
+// Block (32, 8) threads; grid (pair tiles, i tiles, np).
+__global__ void __launch_bounds__(256) pack_phi_kernel(const CDF* __restrict__ acc, const int2* __restrict__ pairs,
+                                                       int n, int np, double2* __restrict__ phi) {
+  __shared__ double2 tile[32][33];
+  const long long P2 = comb2(n), T3 = comb3(n);
+  const long long p0 = (long long)blockIdx.x * 32;
+  const int i0 = blockIdx.y * 32, q = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int iy = ty; iy < 32; iy += 8) {
+    const int i = i0 + iy;
+    const long long pr = p0 + tx;
+    if (i < n && pr < P2) {
+      const CDF v = acc[((long long)i * np + q) * P2 + pr];
+      tile[iy][tx] = make_double2(df_to_double(v.re), df_to_double(v.im));
+    }
+  }
+  __syncthreads();
+  double2* out = phi + (long long)q * T3;
+  for (int py = ty; py < 32; py += 8) {
+    const long long pr = p0 + py;
+    if (pr >= P2) break;
+    const int2 jk = pairs[pr];
+    const int i = i0 + tx;
+    if (i < jk.x) out[triple_rank(i, jk.x, jk.y)] = tile[tx][py];
+  }
 }
 
 struct ElemWs {
   int2* pairs;
   CDF* tab;
-  void *W, *E;
+  void *W, *E;  // plane images of one K chunk (cross products, phases)
   int *eW, *eE;
   CDF* acc;
-  long long ldk;
 };
 
 static ElemWs carve_elem(Arena& ar, const Scheme& sc, int L, int nv, int np) {
   const long long P2 = comb2(nv), R = (long long)nv * np;
   ElemWs w;
-  w.ldk = tc::pad64(EL_KC);
   w.pairs = ar.take<int2>(P2 > 0 ? P2 : 1);
   w.tab = ar.take<CDF>(L);
-  w.W = ar.take<uint16_t>(2LL * sc.na * P2 * w.ldk);
-  w.E = ar.take<uint16_t>(2LL * sc.nb * R * w.ldk);
+  w.W = ar.take<uint16_t>(tc::plane_img_elems(EL_KC, P2, 1, 2 * sc.na));
+  w.E = ar.take<uint16_t>(tc::plane_img_elems(EL_KC, R, 1, 2 * sc.nb));
   w.eW = ar.take<int>(P2 > 0 ? P2 : 1);
   w.eE = ar.take<int>(R);
   w.acc = ar.take<CDF>(P2 * R);
@@ -191,10 +203,9 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
   cfg.err = ctx->d_error;
   for (long long K0 = 0; K0 < Ktot; K0 += EL_KC) {
     const int Kc = (int)((Ktot - K0) < EL_KC ? (Ktot - K0) : EL_KC);
-    DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_pairs", WSrc{vt, w.pairs, V3, (int)K0}, P2, P2, Kc, H, w.W, w.ldk, w.eW, s)));
-    DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_phase", ESrc{vt, w.tab, mom, V3, (int)K0}, R, R, Kc, H, w.E, w.ldk, w.eE, s)));
-    Planes A = planes_of(w.W, Kc, P2, 1, NPLA, w.ldk);
-    Planes B = planes_of(w.E, Kc, R, 1, NPLB, w.ldk);
+    const tc::PlaneImg A = tc::plane_img(w.W, Kc, P2, 1, NPLA), B = tc::plane_img(w.E, Kc, R, 1, NPLB);
+    DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_pairs", WSrc{vt, w.pairs, V3, (int)K0}, P2, A, H, w.eW, s)));
+    DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_phase", ESrc{vt, w.tab, mom, V3, (int)K0}, R, B, H, w.eE, s)));
     cfg.M = (int)P2; cfg.N = (int)R; cfg.K = Kc;
     cfg.a = tc::OpMap{1, 1, 0, 0, 0, (int)P2, w.eW};
     cfg.b = tc::OpMap{1, 1, 0, 0, 0, (int)R, w.eE};
@@ -212,17 +223,19 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
       st = tc::launch_gemm<NTW, 16, NPLA, NPLB, ST, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     } else if (R > 32) {
       epi.nt = 64;
-      st = tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+      st = tc::launch_gemm<64, 16, NPLA, NPLB, tc::max_stages<64, 16, NPLA, NPLB>(), BF16, NACC>(
+          ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     } else {
       epi.nt = 32;
-      st = tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
+      st = tc::launch_gemm<32, 16, NPLA, NPLB, tc::max_stages<32, 16, NPLA, NPLB>(), BF16, NACC>(
+          ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     }
     DISTIL_TRY(st);
   }
   {
-    const long long work = comb3(nv) * mom.np;
     Launch Lz(ctx, "pack_phi", s);
-    pack_phi_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(w.acc, nv, mom.np, phi_t);
+    const dim3 grid((unsigned)((comb2(nv) + 31) / 32), (unsigned)((nv + 31) / 32), (unsigned)mom.np);
+    pack_phi_kernel<<<grid, dim3(32, 8), 0, s>>>(w.acc, w.pairs, nv, mom.np, phi_t);
   }
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;

@@ -23,8 +23,8 @@ size_t cgemm_workspace(int mode, long long M, long long N, long long K, long lon
   const Scheme sc = scheme_of(mode);
   Arena ar;
   ar.take<int>(batch * (M + N));
-  ar.take<uint16_t>(batch * 2 * sc.na * M * tc::pad64(K));
-  ar.take<uint16_t>(batch * 2 * sc.nb * N * tc::pad64(K));
+  ar.take<uint16_t>(tc::plane_img_elems(K, M, batch, 2 * sc.na));
+  ar.take<uint16_t>(tc::plane_img_elems(K, N, batch, 2 * sc.nb));
   return ar.used + 256;
 }
 
@@ -32,12 +32,11 @@ template <bool BF16, bool FIXED, int NA, int NB>
 static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const float2* B, float2* C, int M, int N,
                      int K, int batch, void* ws, size_t ws_bytes, cudaStream_t s) {
   constexpr int NPLA = 2 * NA, NPLB = 2 * NB;
-  const long long ld = tc::pad64(K);
   Arena ar(ws, ws_bytes);
   int* eA = ar.take<int>((long long)batch * M);
   int* eB = ar.take<int>((long long)batch * N);
-  void* PA = ar.take<uint16_t>((long long)batch * NPLA * M * ld);
-  void* PB = ar.take<uint16_t>((long long)batch * NPLB * N * ld);
+  const tc::PlaneImg pa = tc::plane_img(ar.take<uint16_t>(tc::plane_img_elems(K, M, batch, NPLA)), K, M, batch, NPLA);
+  const tc::PlaneImg pb = tc::plane_img(ar.take<uint16_t>(tc::plane_img_elems(K, N, batch, NPLB)), K, N, batch, NPLB);
   if (!ar.fits()) {
     set_error("distil_cgemm: workspace too small");
     return DISTIL_ENOMEM;
@@ -45,8 +44,8 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
   // fixed-point FP16: a narrower leading slice for long K keeps the exact
   // hi*hi sums below 2^24 (they grow like 2^2H sqrt(K) for rows of random sign)
   const int H = (FIXED && !BF16) ? (K <= 1024 ? sch.H : K <= 4096 ? 9 : K <= 16384 ? 8 : 7) : sch.H;
-  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_cgemm", BatchRows{A, K}, (long long)batch * M, M, K, H, PA, ld, eA, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_cgemm", BatchRows{B, K}, (long long)batch * N, N, K, H, PB, ld, eB, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_cgemm", BatchRows{A, K}, (long long)batch * M, pa, H, eA, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_cgemm", BatchRows{B, K}, (long long)batch * N, pb, H, eB, s)));
   tc::GemmCfg cfg{};
   fill_products(cfg, sch);
   cfg.shift = 2 * H;
@@ -54,17 +53,18 @@ static int cgemm_run(distil_ctx* ctx, const Scheme& sch, const float2* A, const 
   cfg.a = tc::OpMap{1, batch, 1, 0, 0, M, eA};
   cfg.b = tc::OpMap{1, batch, 1, 0, 0, N, eB};
   cfg.err = ctx->d_error;
-  tc::Planes pa = planes_of(PA, K, M, batch, NPLA, ld);
-  tc::Planes pb = planes_of(PB, K, N, batch, NPLB, ld);
   EpiStoreC64 epi{{}, C, (long long)M * N, N, N};
   // the 6-product schemes accumulate in three pairs (exact cross terms)
   constexpr int NACC = NPLA == 6 ? 3 : 2;
   constexpr int NTW = NACC == 3 ? 80 : 128;
-  constexpr int ST = (NPLA + NPLB) > 8 ? 2 : 3;
   if (N > 64)
-    return tc::launch_gemm<NTW, 32, NPLA, NPLB, ST, BF16, NACC>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
-  if (N > 32) return tc::launch_gemm<64, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
-  return tc::launch_gemm<32, 32, NPLA, NPLB, 2, BF16, NACC>(ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
+    return tc::launch_gemm<NTW, 16, NPLA, NPLB, tc::max_stages<NTW, 16, NPLA, NPLB>(), BF16, NACC>(
+        ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
+  if (N > 32)
+    return tc::launch_gemm<64, 16, NPLA, NPLB, tc::max_stages<64, 16, NPLA, NPLB>(), BF16, NACC>(
+        ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
+  return tc::launch_gemm<32, 16, NPLA, NPLB, tc::max_stages<32, 16, NPLA, NPLB>(), BF16, NACC>(
+      ctx, "tc_gemm_cgemm", pa, pb, cfg, batch, epi, s);
 }
 
 int cgemm_mixed(distil_ctx* ctx, int mode, const void* A, const void* B, void* C, int M, int N, int K, int batch,

@@ -131,8 +131,8 @@ int distil_plan_create(distil_ctx* ctx, const distil_batch_shape* shape, const d
   if (autotune && mixed) {
     // candidate vectors: every variant of every site appears once (variant 2
     // exists for step i only); each site keeps its fastest
-    constexpr int NC = 5;
-    static const int cand[NC][3] = {{0, 0, 0}, {1, 1, 1}, {2, 3, 3}, {3, 4, 4}, {4, 0, 0}};
+    constexpr int NC = 6;
+    static const int cand[NC][3] = {{0, 0, 0}, {1, 1, 1}, {2, 3, 3}, {3, 4, 4}, {4, 5, 5}, {5, 0, 0}};
     double t[NC][3];
     for (int v = 0; v < NC; ++v) {
       DISTIL_TRY(distil_set_tuning(ctx, cand[v]));

@@ -1,5 +1,5 @@
 // Blackwell (sm_103a) tensor-core primitives written as inline PTX:
-// mbarriers, TMA tensor loads, TMEM allocation, tcgen05.mma (kind::f16),
+// mbarriers, bulk copies, TMEM allocation, tcgen05.mma (kind::f16),
 // tcgen05.commit and tcgen05.ld, plus the shared-memory and instruction
 // descriptors these take.  Every spin-wait here is bounded: on expiry it
 // records an error code in a device word and reports failure to the caller,
@@ -15,7 +15,7 @@ namespace tc {
 
 // ------------------------------------------------------------------ errors
 enum : unsigned {
-  TC_ERR_FULL_WAIT = 1,   // MMA warp gave up waiting for a TMA stage
+  TC_ERR_FULL_WAIT = 1,   // MMA warp gave up waiting for a copied stage
   TC_ERR_EMPTY_WAIT = 2,  // producer gave up waiting for a free stage
   TC_ERR_ACC_WAIT = 3,    // epilogue gave up waiting for the accumulator
   TC_ERR_DRAIN = 4,       // teardown gave up waiting for in-flight copies
@@ -72,17 +72,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
   }
 }
 
-// ------------------------------------------------------------------ TMA
-__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-__device__ __forceinline__ void tma_load_4d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1, int c2,
-                                            int c3) {
+// ------------------------------------------------------------------ bulk copies
+// Global -> shared bulk copy of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned) through the copy engine, completing as transaction bytes
+// on the mbarrier `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// 32-byte global store of w[0..7] (p 32-byte aligned): one whole sector.
+__device__ __forceinline__ void st_global_32B(void* p, const uint32_t (&w)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+               "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
 }
 
 // ------------------------------------------------------------------ TMEM

@@ -3,8 +3,9 @@
 //   D[b](m, n) = sum_k A[b](m, k) * B[b](n, k)          (complex)
 //
 // A and B arrive pre-split: each complex operand is a stack of 2*NA (2*NB)
-// real 16-bit planes (piece p, re/im), K contiguous, read by TMA with the
-// swizzle that matches the K chunk (32/64/128-byte rows).  For every K step
+// real 16-bit planes (piece p, re/im) stored as plane images (PlaneImg: the
+// shared-memory tile image itself, K in blocks of 16), so every stage
+// arrives through plain bulk copies of whole rows of 32 bytes.  For every K step
 // and every product (pa, pb, acc) of the split scheme four MMAs update the
 // accumulator pair `acc` in TMEM:
 //   D_re[acc] += A_re[pa] B_re[pb] + (-A_im[pa]) B_im[pb]   (negate-A descriptor)
@@ -17,8 +18,8 @@
 // all exact powers of two) and hands the leading and the cross-term sums to
 // the functor, which keeps D = D[0] + D[1] as a double-float.
 //
-// One CTA computes a 128 x NT tile: warp 0 issues TMA loads into a STAGES-deep
-// ring, warp 1 allocates TMEM and issues the MMAs, and 8 epilogue warps (two
+// One CTA computes a 128 x NT tile: warp 0 issues the bulk copies of a
+// STAGES-deep ring, warp 1 allocates TMEM and issues the MMAs, and 8 epilogue warps (two
 // per TMEM lane quarter, taking alternate 16-column slices) read the
 // accumulators back (tcgen05.ld) and hand 16-column slices to the epilogue
 // functor.  All waits are bounded (tc.cuh).
@@ -28,6 +29,52 @@
 
 namespace distil {
 namespace tc {
+
+// A stack of 16-bit planes in shared-memory tile-image order.  For
+// coordinate c, K block kb (elements 16 kb .. 16 kb + 15), plane p and row r
+// the 16 elements take 32 contiguous bytes at byte offset
+//   ((((c * kblocks + kb) * planes + p) * rows_pad + r) * 32
+// with their two 16-byte halves swapped where bit 2 of r is set: the
+// 32-byte-swizzled K-major layout the MMA descriptors describe, so the rows
+// r0 .. r0 + R - 1 of one (c, kb, p) (r0 a multiple of 8) are one
+// contiguous run that a single bulk copy puts in place.  Whole cache lines
+// move, where a tensor-map load of 32-byte box rows issued one L2 request
+// per 32-byte sector (the L2 tag rate bounded the contractions).  rows_pad
+// is rows rounded up to 8 plus 128, so any tile starting below `rows` can
+// be copied whole; rows past `rows` only reach outputs that are not kept.
+// Elements of the last K block past K must be zero (the writers store them).
+struct PlaneImg {
+  void* base;
+  long long rows, rows_pad;
+  int K, kblocks, planes, coords;
+  // first row of block (c, kb, p), in rows
+  __host__ __device__ __forceinline__ long long block(long long c, int kb, int p) const {
+    return ((c * kblocks + kb) * planes + p) * rows_pad;
+  }
+  // element index of (c, p, r, k)
+  __host__ __device__ __forceinline__ long long index(long long c, int p, long long r, int k) const {
+    return ((block(c, k >> 4, p) + r) << 4) + ((((k >> 3) ^ (int)(r >> 2)) & 1) << 3) + (k & 7);
+  }
+  __device__ __forceinline__ const uint8_t* rows_at(long long c, int kb, int p, long long r) const {
+    return reinterpret_cast<const uint8_t*>(base) + ((block(c, kb, p) + r) << 5);
+  }
+};
+inline long long img_rows_pad(long long rows) { return (rows + 7) / 8 * 8 + 128; }
+inline PlaneImg plane_img(void* base, long long K, long long rows, long long coords, int planes) {
+  PlaneImg g;
+  g.base = base;
+  g.rows = rows;
+  g.rows_pad = img_rows_pad(rows);
+  g.K = (int)K;
+  g.kblocks = (int)((K + 15) / 16);
+  g.planes = planes;
+  g.coords = (int)coords;
+  return g;
+}
+// 16-bit elements of a plane image
+inline long long plane_img_elems(long long K, long long rows, long long coords, int planes) {
+  return coords * ((K + 15) / 16) * planes * img_rows_pad(rows) * 16;
+}
 
 struct OpMap {
   int bdiv, bmod;   // operand batch coordinate = ((batch / bdiv) % bmod) * bmul + badd
@@ -176,6 +223,7 @@ struct EpiStateless {
 
 template <int NT, int KC, int NPLA, int NPLB>
 struct TileGeom {
+  static_assert(KC == 16, "plane images hold K in blocks of 16");
   static constexpr int SWZ = KC * 2;  // bytes per tile row
   static constexpr int A_PLANE = 128 * SWZ;
   static constexpr int B_PLANE = NT * SWZ;
@@ -200,15 +248,49 @@ constexpr int max_stages() {
 
 constexpr int TC_THREADS = 64 + 8 * 32;  // producer, MMA issuer, 8 epilogue warps
 
+// The NPL planes of K block kb, rows r0 .. r0 + R - 1 of coordinate c, into
+// consecutive R x 32-byte plane tiles at dst: one bulk copy per plane.
+template <int NPL, int R>
+__device__ __forceinline__ void load_planes(const PlaneImg& g, uint8_t* dst, uint64_t* bar, int kb, int c, int r0) {
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) bulk_load(dst + p * (R * 32), g.rows_at(c, kb, p, r0), R * 32, bar);
+}
+template <int NT, int KC, int NPLA, int NPLB>
+__device__ __forceinline__ void load_stage(const PlaneImg& ga, const PlaneImg& gb, uint8_t* sa, uint8_t* sb,
+                                           uint64_t* bar, int kb, int ca, int ra, int cb, int rb) {
+  load_planes<NPLA, 128>(ga, sa, bar, kb, ca, ra);
+  load_planes<NPLB, NT>(gb, sb, bar, kb, cb, rb);
+}
+
+// Exponents of the output tile's row and columns for one epilogue warp,
+// loaded before the accumulator is waited for: ea of the thread's row, and
+// those of the (at most 64) columns of the warp's slices c = half, half + 2,
+// ... packed two per lane: ebp[r] of lane l is column slot 32 r + l, slot
+// 16 s + e being element e of the warp's s-th slice.
+template <int NT>
+__device__ __forceinline__ void tile_exps(const GemmCfg& cfg, int ca, int cb, int row, int n_tile, int half, int lane,
+                                          int& ea, int (&ebp)[2]) {
+  static_assert(NT <= 128, "two column slots per lane");
+  ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int slot = 32 * r + lane, c = half + 2 * (slot >> 4);
+    const int col = n_tile * NT + c * 16 + (slot & 15);
+    ebp[r] = (c < NT / 16 && col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
+  }
+}
+
 // Epilogue of one 16-column slice c of a tile for this thread's row: read
 // the NACC accumulator pairs at TMEM address tl (D0_re | D0_im | D1_re |
 // D1_im [| D2_re | D2_im], NT columns each; every lane of the warp takes
 // part), scale by the exact powers of two 2^(eA + eB - shift) (and w1 for
 // the cross terms, D1 + D2 summed in FP32) and hand the pair to the
-// epilogue functor.
+// epilogue functor.  ea, ebp: tile_exps of this warp (slice c is the
+// warp's slice (c - half) / 2).
 template <int NT, int NACC, class Epi>
 __device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& st, const GemmCfg& cfg, uint32_t tl,
-                                          int c, int batch, int row, int n_tile, int ea, int cb) {
+                                          int c, int half, int batch, int row, int n_tile, int ea,
+                                          const int (&ebp)[2]) {
   uint32_t r0[16], i0[16], r1[16], i1[16], r2[16], i2[16];
   tmem_ld16(tl + c * 16, r0);
   tmem_ld16(tl + NT + c * 16, i0);
@@ -220,13 +302,16 @@ __device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& s
   }
   tmem_wait_ld();
   const int col0 = n_tile * NT + c * 16;
+  const int sl = (c - half) >> 1;                  // the warp's slice index
+  const int ebs = (sl >> 1) ? ebp[1] : ebp[0];     // lane register holding its slots
+  int eb[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) eb[e] = __shfl_sync(0xffffffffu, ebs, ((sl & 1) << 4) + e);
   if (row < cfg.M) {
     float re0[16], re1[16], im0[16], im1[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      const int col = col0 + e;
-      const int eb = (col < cfg.N) ? cfg.b.exp_of(cb, cfg.b.row_off + col) : 0;
-      const float f = pow2f(ea + eb - cfg.shift);  // exact power-of-two scalings
+      const float f = pow2f(ea + eb[e] - cfg.shift);  // exact power-of-two scalings
       const float f1 = f * cfg.w1;
       float x1 = __uint_as_float(r1[e]), y1 = __uint_as_float(i1[e]);
       if constexpr (NACC == 3) {
@@ -244,11 +329,9 @@ __device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& s
 
 template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC, class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   GemmCfg cfg, Epi epi, int n_tiles, int m_tiles) {
+    tc_gemm_kernel(PlaneImg ga, PlaneImg gb, GemmCfg cfg, Epi epi, int n_tiles, int m_tiles) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
   static_assert(NT % 16 == 0 && NT >= 32 && NT <= 128 && 2 * NACC * NT <= 512, "N tile / TMEM columns");
-  static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
   // a CTA of a launch that already hit a timeout does nothing; the epilogue
   // may declare a tile empty (no output it keeps) before anything is set up
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
@@ -279,8 +362,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     *abort_flag = 0;
     *issued_s = 0;
     fence_mbar_init();
-    tma_prefetch(&mapA);
-    tma_prefetch(&mapB);
   }
   if (warp == 1) {
     tmem_alloc(tslot, TCOLS);
@@ -294,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int cb = cfg.b.coord(batch);
 
   if (warp == 0 && lane == 0) {
-    // ---------------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------------- copy producer
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
@@ -304,8 +385,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       mbar_arrive_expect_tx(&full[s], G::STAGE);
-      tma_load_4d(&mapA, &full[s], sA + s * G::A_STAGE, kb * KC, m_tile * 128 + cfg.a.row_off, 0, ca);
-      tma_load_4d(&mapB, &full[s], sB + s * G::B_STAGE, kb * KC, n_tile * NT + cfg.b.row_off, 0, cb);
+      load_stage<NT, KC, NPLA, NPLB>(ga, gb, sA + s * G::A_STAGE, sB + s * G::B_STAGE, &full[s], kb, ca,
+                                     m_tile * 128 + cfg.a.row_off, cb, n_tile * NT + cfg.b.row_off);
       ++issued;
     }
     *(volatile uint32_t*)issued_s = issued;
@@ -346,17 +427,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;             // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;   // which half of the NT columns
+    const int row = m_tile * 128 + q * 32 + lane;
+    int ea, ebp[2];
+    tile_exps<NT>(cfg, ca, cb, row, n_tile, half, lane, ea, ebp);
     bool ok = mbar_wait(accf, 0, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
     ok = __all_sync(0xffffffffu, ok && !*(volatile uint32_t*)abort_flag);  // warp-uniform for tcgen05.ld
     tc_fence_after();
     if (ok) {
       typename Epi::State st;
       epi.begin(st);
-      const int row = m_tile * 128 + q * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-      const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = half; c < NT / 16; c += 2) epi_slice<NT, NACC>(epi, st, cfg, tl, c, batch, row, n_tile, ea, cb);
+      for (int c = half; c < NT / 16; c += 2)
+        epi_slice<NT, NACC>(epi, st, cfg, tl, c, half, batch, row, n_tile, ea, ebp);
       epi.end(st, batch);
     }
     tc_fence_before();
@@ -385,21 +468,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Persistent variant for short contractions (K of a few hundred), where the
 // epilogue costs as much as the MMAs: one CTA per SM walks the tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ... (same tile order as the one-tile
-// kernel's grid: n fastest, then m, then batch).  TMEM holds two
-// accumulator sets (2 x 4 NT columns), so the MMA warp fills one while the
-// epilogue warps drain the other; the TMA ring runs on across tiles.
-//   full[s] / empty[s]   TMA ring (producer <-> MMA)
+// kernel's grid: n fastest, then m, then batch).  TMEM holds NSETS
+// accumulator sets of 2 NACC NT columns.  With two, the MMA warp fills one
+// while the epilogue warps drain the other; with one (128-wide tiles, whose
+// MMAs read half the shared-memory bytes per flop of 64-wide ones), the
+// MMAs of a tile wait for the epilogue of the previous one while the copy
+// ring already fills with the next tile's operands.  The ring runs on
+// across tiles either way.
+//   full[s] / empty[s]   copy ring (producer <-> MMA)
 //   tfull[b]             MMA -> epilogue: accumulator set b is complete
 //   tempty[b]            epilogue -> MMA: set b has been read (8 warp arrivals)
 // Every wait is bounded; on expiry the error word is set, every role leaves
 // its loop, copies still in flight are waited for and TMEM is freed.
-template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC, class Epi>
+template <int NT, int KC, int NPLA, int NPLB, int STAGES, bool BF16, int NACC, class Epi, int NSETS = 2>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                              GemmCfg cfg, Epi epi, int n_tiles, int m_tiles, int total_tiles) {
+    tc_gemm_persistent_kernel(PlaneImg ga, PlaneImg gb, GemmCfg cfg, Epi epi, int n_tiles, int m_tiles,
+                              int total_tiles) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
-  static_assert(NT % 16 == 0 && NT >= 32 && 4 * NACC * NT <= 512, "two accumulator sets must fit TMEM");
-  static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
+  static_assert(NSETS == 1 || NSETS == 2, "one or two accumulator sets");
+  static_assert(NT % 16 == 0 && NT >= 32 && NT <= 256 && NSETS * 2 * NACC * NT <= 512,
+                "the accumulator sets must fit TMEM");
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -417,14 +505,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (cfg.K + KC - 1) / KC;
   constexpr uint32_t SET = 2 * NACC * NT;  // D0_re | D0_im | D1_re | D1_im [| D2_re | D2_im]
-  constexpr uint32_t TCOLS = tmem_alloc_cols(2 * SET);
+  constexpr uint32_t TCOLS = tmem_alloc_cols(NSETS * SET);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NSETS; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 8);
     }
@@ -432,8 +520,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     *abort_flag = 0;
     *issued_s = 0;
     fence_mbar_init();
-    tma_prefetch(&mapA);
-    tma_prefetch(&mapB);
   }
   if (warp == 1) {
     tmem_alloc(tslot, TCOLS);
@@ -446,7 +532,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile uint32_t* abort_v = abort_flag;
 
   if (warp == 0 && lane == 0) {
-    // ---------------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------------- copy producer
     uint32_t g = 0;
     for (int t = blockIdx.x; t < total_tiles && !*abort_v; t += gridDim.x) {
       const TileIdx ti = tile_at(t, n_tiles, m_tiles, cfg);
@@ -461,8 +547,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[s], G::STAGE);
-        tma_load_4d(&mapA, &full[s], sA + s * G::A_STAGE, kb * KC, m_tile * 128 + cfg.a.row_off, 0, ca);
-        tma_load_4d(&mapB, &full[s], sB + s * G::B_STAGE, kb * KC, n_tile * NT + cfg.b.row_off, 0, cb);
+        load_stage<NT, KC, NPLA, NPLB>(ga, gb, sA + s * G::A_STAGE, sB + s * G::B_STAGE, &full[s], kb, ca,
+                                       m_tile * 128 + cfg.a.row_off, cb, n_tile * NT + cfg.b.row_off);
         *(volatile uint32_t*)issued_s = g + 1;
       }
     }
@@ -476,7 +562,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const TileIdx ti = tile_at(t, n_tiles, m_tiles, cfg);
       const int n_tile = ti.n_tile, m_tile = ti.m_tile, batch = ti.batch;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
-      const uint32_t buf = it & 1, use = it >> 1;
+      const uint32_t buf = it % NSETS, use = it / NSETS;
       if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait) || *abort_v) {
         *abort_v = 1;
         break;
@@ -523,7 +609,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const TileIdx ti = tile_at(t, n_tiles, m_tiles, cfg);
       const int n_tile = ti.n_tile, m_tile = ti.m_tile, batch = ti.batch;
       if (epi.skip_tile(m_tile, n_tile, batch)) continue;
-      const uint32_t buf = it & 1, use = it >> 1;
+      const uint32_t buf = it % NSETS, use = it / NSETS;
+      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
+      const int row = m_tile * 128 + q * 32 + lane;
+      int ea, ebp[2];
+      tile_exps<NT>(cfg, ca, cb, row, n_tile, half, lane, ea, ebp);
       bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
       ok = __all_sync(0xffffffffu, ok && !*abort_v);  // warp-uniform for tcgen05.ld
       if (!ok) {
@@ -531,14 +621,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
       typename Epi::State st;
       epi.begin(st);
-      const int row = m_tile * 128 + q * 32 + lane;
       const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
-      const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = half; c < NT / 16; c += 2) epi_slice<NT, NACC>(epi, st, cfg, tl, c, batch, row, n_tile, ea, cb);
+      for (int c = half; c < NT / 16; c += 2)
+        epi_slice<NT, NACC>(epi, st, cfg, tl, c, half, batch, row, n_tile, ea, ebp);
       epi.end(st, batch);
       // this warp is done reading set buf: hand it back to the MMA warp
       tc_fence_before();
@@ -577,11 +665,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 //   afree   MMA -> producer: every MMA reading the resident A has completed
 template <int NT, int KC, int NPLA, int NPLB, int NKA, int STAGES, bool BF16, int NACC, class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_ares_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                        GemmCfg cfg, Epi epi, int n_tiles, int m_tiles, int total_tiles) {
+    tc_gemm_ares_kernel(PlaneImg ga, PlaneImg gb, GemmCfg cfg, Epi epi, int n_tiles, int m_tiles,
+                        int total_tiles) {
   using G = TileGeom<NT, KC, NPLA, NPLB>;
   static_assert(NT % 16 == 0 && NT >= 32 && 4 * NACC * NT <= 512, "two accumulator sets must fit TMEM");
-  static_assert(KC == 16 || KC == 32 || KC == 64, "K chunk");
   if (cfg.err && *(volatile unsigned*)cfg.err) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -623,8 +710,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     *issued_s = 0;
     *aloads_s = 0;
     fence_mbar_init();
-    tma_prefetch(&mapA);
-    tma_prefetch(&mapB);
   }
   if (warp == 1) {
     tmem_alloc(tslot, TCOLS);
@@ -637,7 +722,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile uint32_t* abort_v = abort_flag;
 
   if (warp == 0 && lane == 0) {
-    // ---------------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------------- copy producer
     uint32_t g = 0, reloads = 0;
     int key = -1;
     for (int t = t_begin; t < t_end && !*abort_v; ++t) {
@@ -651,7 +736,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int ca = cfg.a.coord(batch);
         mbar_arrive_expect_tx(afull, nk * G::A_STAGE);
         for (int kb = 0; kb < nk; ++kb)
-          tma_load_4d(&mapA, afull, sA + kb * G::A_STAGE, kb * KC, m_tile * 128 + cfg.a.row_off, 0, ca);
+          load_planes<NPLA, 128>(ga, sA + kb * G::A_STAGE, afull, kb, ca, m_tile * 128 + cfg.a.row_off);
         ++reloads;
         *(volatile uint32_t*)aloads_s = reloads;
         key = rest;
@@ -667,7 +752,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[s], G::B_STAGE);
-        tma_load_4d(&mapB, &full[s], sB + s * G::B_STAGE, kb * KC, n_tile * NT + cfg.b.row_off, 0, cb);
+        load_planes<NPLB, NT>(gb, sB + s * G::B_STAGE, &full[s], kb, cb, n_tile * NT + cfg.b.row_off);
         *(volatile uint32_t*)issued_s = g + 1;
       }
       if (!ok) break;
@@ -736,6 +821,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = t_begin; t < t_end; ++t) {
       const int n_tile = t % n_tiles, rest = t / n_tiles, m_tile = rest % m_tiles, batch = rest / m_tiles;
       const uint32_t buf = it & 1, use = it >> 1;
+      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
+      const int row = m_tile * 128 + q * 32 + lane;
+      int ea, ebp[2];
+      tile_exps<NT>(cfg, ca, cb, row, n_tile, half, lane, ea, ebp);
       bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
       ok = __all_sync(0xffffffffu, ok && !*abort_v);
       if (!ok) {
@@ -743,14 +832,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int ca = cfg.a.coord(batch), cb = cfg.b.coord(batch);
       typename Epi::State st;
       epi.begin(st);
-      const int row = m_tile * 128 + q * 32 + lane;
       const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
-      const int ea = (row < cfg.M) ? cfg.a.exp_of(ca, cfg.a.row_off + row) : 0;
 #pragma unroll 1
-      for (int c = half; c < NT / 16; c += 2) epi_slice<NT, NACC>(epi, st, cfg, tl, c, batch, row, n_tile, ea, cb);
+      for (int c = half; c < NT / 16; c += 2)
+        epi_slice<NT, NACC>(epi, st, cfg, tl, c, half, batch, row, n_tile, ea, ebp);
       epi.end(st, batch);
       tc_fence_before();
       __syncwarp();

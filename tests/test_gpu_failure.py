@@ -4,7 +4,7 @@ The tensor-core pipelines wait on mbarriers with a bounded number of clock
 cycles; on expiry a kernel records a code in the context's device word and
 returns, and later tensor-core launches of the context return at once until
 the word is reset.  These tests make a wait expire on purpose with a tiny
-limit (the MMA warp gives up before its first TMA stage lands; the copies
+limit (the MMA warp gives up before its first copied stage lands; the copies
 and MMAs in flight are still waited for, with the long limit, before the
 CTA exits), check that distil_device_status reports it, that a reset clears
 it and that the next call with the normal limit is correct.  Input scans and
@@ -41,7 +41,7 @@ def test_expired_wait_is_reported_and_cleared(cuda_lib):
     ref = A.astype(np.complex128) @ B.astype(np.complex128).T
     assert _status(L, ctx, True) == (0, 0)
     try:
-        distil.set_wait_limit(64)          # far shorter than a TMA round trip
+        distil.set_wait_limit(64)          # far shorter than a bulk-copy round trip
         distil.cgemm(T(A), T(B), "fp16x6")
         st, code = _status(L, ctx, False)
         assert st == 4 and code in (1, 2, 3), (st, code)     # DISTIL_ETIMEOUT, a pipeline wait

@@ -45,7 +45,7 @@ def test_plan_uneven_ensemble_mixed(cuda_lib, autotune):
     cfgs = device_cfgs(ens)
     plan = distil.Plan(4, 3, MOM, 2, 1, "fp16x6", cfgs, autotune=autotune)
     variants, kernels = plan.info()
-    assert variants[0] in range(5) and variants[1] in (0, 1, 3, 4) and variants[2] in (0, 1, 3, 4)
+    assert variants[0] in range(6) and variants[1] in (0, 1, 3, 4, 5) and variants[2] in (0, 1, 3, 4, 5)
     assert kernels > 10 * len(cfgs)
     assert distil.get_tuning() == variants
     plan.run()
@@ -83,7 +83,8 @@ def test_tuning_variants_give_identical_results(cuda_lib):
     saved = distil.get_tuning()
     try:
         outs = []
-        for var in ([0, 0, 0], [1, 1, 1], [1, 0, 1], [2, 0, 1], [2, 1, 0], [3, 3, 3], [4, 4, 4], [0, 4, 3]):
+        for var in ([0, 0, 0], [1, 1, 1], [1, 0, 1], [2, 0, 1], [2, 1, 0], [3, 3, 3], [4, 4, 4], [0, 4, 3], [5, 5, 5],
+                    [5, 1, 0]):
             distil.set_tuning(var)
             outs.append(distil.correlate(phi, phi[0], tau, T(p.prof), "fp16x6").cpu().numpy())
     finally:
