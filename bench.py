@@ -948,9 +948,14 @@ def kernel_rooflines(kstats, p, mode, pk, steps):
 def split_products(mode, kernel=None) -> int:
     """Real 16-bit products per complex MAC pair the tensor-core kernels issue:
     the FP16X6 elementals keep eight split products, the other FP16X6 and
-    BF16X6 contractions six, the X3 modes three."""
+    BF16X6 contractions six, the X3 modes three.  The six-product step-j and
+    T contractions run as two passes of three (leading classes, then the
+    second-order terms: kernels <name> and <name>_2nd)."""
     if mode == "fp16x6" and kernel == "tc_gemm_elementals":
         return 8
+    six = mode in ("fp16x6", "bf16x6")
+    if six and kernel in ("tc_gemm_step_j", "tc_gemm_tcontract", "tc_gemm_step_j_2nd", "tc_gemm_tcontract_2nd"):
+        return 3
     return {"bf16x6": 6, "bf16x3": 3, "fp16x3": 3, "fp16x6": 6}[mode]
 
 
@@ -962,8 +967,11 @@ def kernel_cmacs(name, p):
     table = {
         "tc_gemm_step_i": (12.0 * nb * n ** 4 * tp, "12 N_B N_v^4 per (t,p): i contraction, 12 spin blocks, all (k,j)"),
         "tc_gemm_step_j": (24.0 * nb * n ** 4 * tp, "24 N_B N_v^4 per (t,p): j contraction, 6 spin pairs, K = 4 N_v"),
+        "tc_gemm_step_j_2nd": (24.0 * nb * n ** 4 * tp, "24 N_B N_v^4 per (t,p): second-order pass of step j"),
         "tc_gemm_tcontract": (5.0 * nb * P2 * n * n * tp,
                               "5 N_B C(N_v,2) N_v^2 per (t,p): T^c contraction of W, K = 5 N_v"),
+        "tc_gemm_tcontract_2nd": (5.0 * nb * P2 * n * n * tp,
+                                  "5 N_B C(N_v,2) N_v^2 per (t,p): second-order pass of the T contraction"),
         "tc_gemm_elementals": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p): useful i<j<k MACs"),
         "elementals_simt_f32": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p)"),
         "elementals_simt_f64": (3.0 * p.V3 * p.T3 * tp, "3 V3 C(N_v,3) per (t,p)"),

@@ -248,10 +248,10 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::Pla
 // elements only): one thread per (coordinate, plane, row).
 static __global__ void img_zero_kpad_kernel(tc::PlaneImg img) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long rows = (long long)img.coords * img.planes * img.rows;
+  const long long rows = (long long)img.coords * img.ptot * img.rows;
   if (t >= rows) return;
-  const long long c = t / ((long long)img.planes * img.rows);
-  const int p = (int)((t / img.rows) % img.planes);
+  const long long c = t / ((long long)img.ptot * img.rows);
+  const int p = (int)((t / img.rows) % img.ptot);
   const long long r = t % img.rows;
   uint16_t* out = reinterpret_cast<uint16_t*>(img.base);
   for (int k = img.K; k < img.kblocks * 16; ++k) out[img.index(c, p, r, k)] = 0;
@@ -261,7 +261,8 @@ template <bool BF16, bool FIXED, int NPC, class Src>
 inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long long nrows, const tc::PlaneImg& img,
                       int H, int* exps, cudaStream_t s, float* norms = nullptr) {
   if (nrows <= 0) return DISTIL_OK;
-  if (img.planes != 2 * NPC || nrows > (long long)img.coords * img.rows || img.kblocks * 16 < img.K) {
+  if (img.planes != 2 * NPC || img.ptot != img.planes || nrows > (long long)img.coords * img.rows ||
+      img.kblocks * 16 < img.K) {
     set_error("%s: rows or planes outside the plane image", name);
     return DISTIL_EINVAL;
   }
@@ -281,7 +282,7 @@ inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long lo
 
 inline int img_zero_kpad(distil_ctx* ctx, const tc::PlaneImg& img, cudaStream_t s) {
   if (img.kblocks * 16 == img.K) return DISTIL_OK;
-  const long long rows = (long long)img.coords * img.planes * img.rows;
+  const long long rows = (long long)img.coords * img.ptot * img.rows;
   Launch L(ctx, "img_zero_kpad", s);
   img_zero_kpad_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(img);
   DISTIL_LAUNCH_CHECK();
@@ -337,6 +338,30 @@ struct EpiStoreCDF : tc::EpiStateless {
       const int c = col0 + e;
       if (c >= N) break;
       if (cm.keep(c)) base[cm(c)] = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
+    }
+  }
+};
+
+// out[batch][row * sr + colmap(col)] += D (complex double-float): the
+// second pass of a contraction split by accumulator class.
+struct EpiAddCDF : tc::EpiStateless {
+  CDF* out;
+  long long sb_hi, sb_lo;
+  int b_lo;
+  long long sr;
+  ColMap cm;
+  int N;
+  __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
+  __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
+                                             const float* im0, const float* im1) const {
+    CDF* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int c = col0 + e;
+      if (c >= N) break;
+      if (!cm.keep(c)) continue;
+      CDF* d = base + cm(c);
+      *d = cdf_add(*d, cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e])));
     }
   }
 };

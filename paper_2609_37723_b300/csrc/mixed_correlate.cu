@@ -628,6 +628,17 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const PlaneImg
   constexpr int NTP = NACC == 3 ? 32 : 64;    // persistent: two sets of 2 NACC NT columns
   constexpr int NTW = NACC == 3 ? 80 : 128;   // one-tile: 2 NACC NT columns
   const int var = ctx->tune[site];
+  if constexpr (NACC == 1) {
+    // the second-order pass of a split contraction: two 128-wide sets
+    // (2 x 2 x 128 TMEM columns), the epilogue of one tile under the MMAs
+    // of the next
+    (void)var;
+    if (cfg.N > 64)
+      return tc::launch_gemm_persistent<128, KC, NPLA, NPLB, tc::max_stages<128, KC, NPLA, NPLB>(), BF16, 1, 2>(
+          ctx, name, A, B, cfg, batch, epi, s);
+    return tc::launch_gemm_persistent<64, KC, NPLA, NPLB, tc::max_stages<64, KC, NPLA, NPLB>(), BF16, 1, 2>(
+        ctx, name, A, B, cfg, batch, epi, s);
+  } else {
   if (var == 5 && cfg.N > 64) {
     if constexpr (NACC == 3) {
       const double c80 = ((cfg.N + 79) / 80) * 80 * (1.0 / 80 + 1.0 / 128);
@@ -673,6 +684,38 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const PlaneImg
                                                                                                 batch, epi, s);
   return tc::launch_gemm<32, KC, NPLA, NPLB, tc::max_stages<32, KC, NPLA, NPLB>(), BF16, NACC>(ctx, name, A, B, cfg,
                                                                                               batch, epi, s);
+  }
+}
+
+// A long contraction of the 3 x 4 piece schemes in two passes over the same
+// plane images, so that no pass needs more than two accumulator pairs and
+// the MMAs run 128 wide (three pairs fit TMEM only 80 wide, and 80-wide
+// MMAs take ~1.3x the time per column):
+//   pass A  the leading two pieces of each side (the first four planes):
+//           hi*hi | hi*mid + mid*hi, both pairs exact integer sums, stored
+//           by epi as D0 + D1;
+//   pass B  the second-order terms hi*lo, mid*mid', lo*hi in one pair,
+//           added into the stored values in double-float by epi_add.
+// The classes accumulate exactly as with three pairs; D1 and D2 now meet in
+// double-float instead of FP32.
+template <bool BF16, class EpiS, class EpiA>
+static int contract_two_pass(distil_ctx* ctx, GemmSite site, const char* name, const char* name_2nd,
+                             const PlaneImg& A, const PlaneImg& B, tc::GemmCfg cfg, int batch, const EpiS& epi,
+                             const EpiA& epi_add, cudaStream_t s) {
+  using PA = tc::SchemeProducts<4, 4, 2>;
+  cfg.nprod = PA::n;
+  for (int p = 0; p < PA::n; ++p) {
+    cfg.pa[p] = PA::pa[p];
+    cfg.pb[p] = PA::pb[p];
+  }
+  DISTIL_TRY((gemm<BF16, 4, 4, 2>(ctx, site, name, tc::first_planes(A, 4), tc::first_planes(B, 4), cfg, batch, epi, s)));
+  using PB = tc::SchemeProducts<6, 8, 1>;
+  cfg.nprod = PB::n;
+  for (int p = 0; p < PB::n; ++p) {
+    cfg.pa[p] = PB::pa[p];
+    cfg.pb[p] = PB::pb[p];
+  }
+  return gemm<BF16, 6, 8, 1>(ctx, site, name_2nd, A, B, cfg, batch, epi_add, s);
 }
 
 static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
@@ -743,7 +786,12 @@ static int run_group_mixed(distil_ctx* ctx, const Scheme& sch, int pb, const dou
     epi.out = w.V + (long long)slotbase[ap] * n3;
     epi.b_lo = 1; epi.sb_hi = NPAIR * n3; epi.sb_lo = 0;
     epi.sr = 1; epi.cm = ColMap{n2, nvp, n3, nv}; epi.N = (3 - ap) * nvp;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_STEP_J, "tc_gemm_step_j", w.U, w.TT, cfg, (int)bq, epi, s)));
+    if constexpr (NPLA == 6) {
+      const EpiAddCDF add{{}, epi.out, epi.sb_hi, epi.sb_lo, epi.b_lo, epi.sr, epi.cm, epi.N};
+      DISTIL_TRY((contract_two_pass<BF16>(ctx, SITE_STEP_J, "tc_gemm_step_j", "tc_gemm_step_j_2nd", w.U, w.TT, cfg, (int)bq, epi, add, s)));
+    } else {
+      DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_STEP_J, "tc_gemm_step_j", w.U, w.TT, cfg, (int)bq, epi, s)));
+    }
   }
   // ---- W: the source-weighted antisymmetric parts of V, split (rows (momentum, a, pair), K = (c, k))
   {
@@ -766,7 +814,12 @@ static int run_group_mixed(distil_ctx* ctx, const Scheme& sch, int pb, const dou
     epi.out = w.Z;
     epi.b_lo = 1; epi.sb_hi = P2 * n; epi.sb_lo = 0;
     epi.sr = n; epi.cm = ColMap{1, 0, 0, 0}; epi.N = nv;
-    DISTIL_TRY((gemm<BF16, NPLA, NPLB, (NPLA == 6 ? 3 : 2)>(ctx, SITE_SOURCE, "tc_gemm_tcontract", w.W, w.TcT, cfg, (int)bq, epi, s)));
+    if constexpr (NPLA == 6) {
+      const EpiAddCDF add{{}, epi.out, epi.sb_hi, epi.sb_lo, epi.b_lo, epi.sr, epi.cm, epi.N};
+      DISTIL_TRY((contract_two_pass<BF16>(ctx, SITE_SOURCE, "tc_gemm_tcontract", "tc_gemm_tcontract_2nd", w.W, w.TcT, cfg, (int)bq, epi, add, s)));
+    } else {
+      DISTIL_TRY((gemm<BF16, NPLA, NPLB, 2>(ctx, SITE_SOURCE, "tc_gemm_tcontract", w.W, w.TcT, cfg, (int)bq, epi, s)));
+    }
   }
   // ---- dot, then the fixed-order reduction into C (momentum on grid y)
   {

@@ -210,7 +210,7 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
     cfg.a = tc::OpMap{1, 1, 0, 0, 0, (int)P2, w.eW};
     cfg.b = tc::OpMap{1, 1, 0, 0, 0, (int)R, w.eE};
     EpiPhiAcc epi{{}, w.acc, w.pairs, P2, (int)R, mom.np, K0 == 0 ? 1 : 0, 128};
-    // K = 4096 per chunk: a deep ring of 16-wide K steps keeps enough of the
+    // K = 4032 per chunk: a deep ring of 16-wide K steps keeps enough of the
     // operand stream (the A pieces come from HBM) in flight.  The 6-product
     // schemes accumulate in three pairs (exact cross terms), which leaves
     // TMEM room for 80-wide N tiles.
@@ -220,6 +220,9 @@ static int elem_t(distil_ctx* ctx, const Scheme& sch, int H, const float2* vt, i
     int st;
     if (R > 64) {
       epi.nt = NTW;
+      // one tile per CTA: the hardware hands out the tiles that survive the
+      // triangle skip as SMs free up (a persistent kernel's static tile
+      // assignment balanced them worse: 531 against 481 ms per L = 48 step)
       st = tc::launch_gemm<NTW, 16, NPLA, NPLB, ST, BF16, NACC>(ctx, "tc_gemm_elementals", A, B, cfg, 1, epi, s);
     } else if (R > 32) {
       epi.nt = 64;

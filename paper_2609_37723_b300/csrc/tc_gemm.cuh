@@ -43,13 +43,15 @@ namespace tc {
 // is rows rounded up to 8 plus 128, so any tile starting below `rows` can
 // be copied whole; rows past `rows` only reach outputs that are not kept.
 // Elements of the last K block past K must be zero (the writers store them).
+// An image stores ptot planes per (c, kb); a GEMM reads its first `planes`
+// (first_planes: the leading pieces only).
 struct PlaneImg {
   void* base;
   long long rows, rows_pad;
-  int K, kblocks, planes, coords;
+  int K, kblocks, planes, coords, ptot;
   // first row of block (c, kb, p), in rows
   __host__ __device__ __forceinline__ long long block(long long c, int kb, int p) const {
-    return ((c * kblocks + kb) * planes + p) * rows_pad;
+    return ((c * kblocks + kb) * ptot + p) * rows_pad;
   }
   // element index of (c, p, r, k)
   __host__ __device__ __forceinline__ long long index(long long c, int p, long long r, int k) const {
@@ -69,7 +71,14 @@ inline PlaneImg plane_img(void* base, long long K, long long rows, long long coo
   g.kblocks = (int)((K + 15) / 16);
   g.planes = planes;
   g.coords = (int)coords;
+  g.ptot = planes;
   return g;
+}
+// The same image read as its first np planes.
+inline PlaneImg first_planes(const PlaneImg& g, int np) {
+  PlaneImg v = g;
+  v.planes = np;
+  return v;
 }
 // 16-bit elements of a plane image
 inline long long plane_img_elems(long long K, long long rows, long long coords, int planes) {
@@ -157,6 +166,20 @@ struct SchemeProducts<8, 8, 3> {
   static constexpr int n = 8;
   static constexpr int pa[8] = {0, 0, 1, 0, 3, 1, 3, 2}, pb[8] = {0, 1, 0, 3, 0, 2, 2, 3},
                        acc[8] = {0, 1, 1, 2, 2, 2, 2, 2};
+};
+// The second-order class alone (one accumulator pair), for a second pass
+// over the same operands after <4, 4, 2> has accumulated hi*hi | hi*mid +
+// mid*hi from the leading two pieces of each side: 3 x 4 pieces (the
+// <6, 8, 3> products of pair 2) and 4 x 4 pieces (those of <8, 8, 3>).
+template <>
+struct SchemeProducts<6, 8, 1> {
+  static constexpr int n = 3;
+  static constexpr int pa[3] = {0, 1, 2}, pb[3] = {3, 2, 0}, acc[3] = {0, 0, 0};
+};
+template <>
+struct SchemeProducts<8, 8, 1> {
+  static constexpr int n = 5;
+  static constexpr int pa[5] = {0, 3, 1, 3, 2}, pb[5] = {3, 0, 2, 2, 3}, acc[5] = {0, 0, 0, 0, 0};
 };
 template <>
 struct SchemeProducts<4, 4, 2> {
@@ -294,8 +317,10 @@ __device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& s
   uint32_t r0[16], i0[16], r1[16], i1[16], r2[16], i2[16];
   tmem_ld16(tl + c * 16, r0);
   tmem_ld16(tl + NT + c * 16, i0);
-  tmem_ld16(tl + 2 * NT + c * 16, r1);
-  tmem_ld16(tl + 3 * NT + c * 16, i1);
+  if constexpr (NACC >= 2) {
+    tmem_ld16(tl + 2 * NT + c * 16, r1);
+    tmem_ld16(tl + 3 * NT + c * 16, i1);
+  }
   if constexpr (NACC == 3) {
     tmem_ld16(tl + 4 * NT + c * 16, r2);
     tmem_ld16(tl + 5 * NT + c * 16, i2);
@@ -313,15 +338,23 @@ __device__ __forceinline__ void epi_slice(const Epi& epi, typename Epi::State& s
     for (int e = 0; e < 16; ++e) {
       const float f = pow2f(ea + eb[e] - cfg.shift);  // exact power-of-two scalings
       const float f1 = f * cfg.w1;
-      float x1 = __uint_as_float(r1[e]), y1 = __uint_as_float(i1[e]);
-      if constexpr (NACC == 3) {
-        x1 += __uint_as_float(r2[e]);
-        y1 += __uint_as_float(i2[e]);
+      if constexpr (NACC == 1) {
+        // a pass of cross terms only: its one pair carries the w1 weight
+        re0[e] = 0.f;
+        im0[e] = 0.f;
+        re1[e] = __uint_as_float(r0[e]) * f1;
+        im1[e] = __uint_as_float(i0[e]) * f1;
+      } else {
+        float x1 = __uint_as_float(r1[e]), y1 = __uint_as_float(i1[e]);
+        if constexpr (NACC == 3) {
+          x1 += __uint_as_float(r2[e]);
+          y1 += __uint_as_float(i2[e]);
+        }
+        re0[e] = __uint_as_float(r0[e]) * f;
+        im0[e] = __uint_as_float(i0[e]) * f;
+        re1[e] = x1 * f1;
+        im1[e] = y1 * f1;
       }
-      re0[e] = __uint_as_float(r0[e]) * f;
-      im0[e] = __uint_as_float(i0[e]) * f;
-      re1[e] = x1 * f1;
-      im1[e] = y1 * f1;
     }
     epi(st, batch, row, col0, re0, re1, im0, im1);
   }
