@@ -145,9 +145,11 @@ __device__ __forceinline__ void make_pieces(DF x, Pow2 s, typename tc::Piece<BF1
 }
 
 // Pieces of element v at K index k of row rr of coordinate c into the 2 NPC
-// planes of img (plane 2 i + re/im holds piece i).  Lanes with consecutive k
-// fill whole 32-byte rows of a K block together.
-template <bool BF16, bool FIXED, int NPC>
+// planes of img: piece i in the planes 2 ((i + ROT) mod NPC) + re/im (ROT = 2
+// with four pieces stores them in the order mid', lo, hi, mid, for the
+// two-pass contractions).  Lanes with consecutive k fill whole 32-byte rows
+// of a K block together.
+template <bool BF16, bool FIXED, int NPC, int ROT = 0>
 __device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long c, long long rr, int k, const CDF& v,
                                              Pow2 sc) {
   using P16 = typename tc::Piece<BF16>::T;
@@ -158,8 +160,9 @@ __device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long 
   const long long ps = img.rows_pad * 16;  // plane stride in elements
 #pragma unroll
   for (int i = 0; i < NPC; ++i) {
-    out[(2 * i) * ps] = pr[i];
-    out[(2 * i + 1) * ps] = pi[i];
+    const int slot = (i + ROT) % NPC;
+    out[(2 * slot) * ps] = pr[i];
+    out[(2 * slot + 1) * ps] = pi[i];
   }
 }
 
@@ -171,7 +174,7 @@ __device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long 
 // into norms[r].  One warp per row: pass 1 finds max |re|, |im| over the
 // row, pass 2 writes the pieces.  Src::operator()(r, k) returns the element
 // as a complex double-float, Src::approx(r, k) an FP32 estimate of it.
-template <bool BF16, bool FIXED, int NPC, class Src>
+template <bool BF16, bool FIXED, int NPC, class Src, int ROT = 0>
 __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, tc::PlaneImg img, int H,
                                                          int* __restrict__ exps, float* __restrict__ norms) {
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -197,13 +200,13 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   const Pow2 sc = pow2_pair(H - e);
   const long long coord = r / img.rows, rr = r % img.rows;
   for (int k = lane; k < Kp; k += 32)
-    store_pieces<BF16, FIXED, NPC>(img, coord, rr, k, k < K ? src(r, k) : cdf_zero(), sc);
+    store_pieces<BF16, FIXED, NPC, ROT>(img, coord, rr, k, k < K ? src(r, k) : cdf_zero(), sc);
 }
 
 // Long rows (K <= 512 PER): one block of 512 threads per row, each thread
 // holding PER elements in registers, so every element is formed once and
 // the exponent comes from the exact maximum.
-template <bool BF16, bool FIXED, int NPC, int PER, class Src>
+template <bool BF16, bool FIXED, int NPC, int PER, class Src, int ROT = 0>
 __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::PlaneImg img, int H,
                                                                 int* __restrict__ exps, float* __restrict__ norms) {
   __shared__ float red_m[16], red_s[16];
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::Pla
   for (int u = 0; u < PER; ++u) {
     const int k = threadIdx.x + 512 * u;
     if (k >= Kp) break;
-    store_pieces<BF16, FIXED, NPC>(img, coord, rr, k, v[u], sc);
+    store_pieces<BF16, FIXED, NPC, ROT>(img, coord, rr, k, v[u], sc);
   }
 }
 
@@ -257,11 +260,11 @@ static __global__ void img_zero_kpad_kernel(tc::PlaneImg img) {
   for (int k = img.K; k < img.kblocks * 16; ++k) out[img.index(c, p, r, k)] = 0;
 }
 
-template <bool BF16, bool FIXED, int NPC, class Src>
+template <bool BF16, bool FIXED, int NPC, class Src, int ROT = 0>
 inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long long nrows, const tc::PlaneImg& img,
                       int H, int* exps, cudaStream_t s, float* norms = nullptr) {
   if (nrows <= 0) return DISTIL_OK;
-  if (img.planes != 2 * NPC || img.ptot != img.planes || nrows > (long long)img.coords * img.rows ||
+  if (img.planes != 2 * NPC || img.ptot != img.planes || img.p0 != 0 || nrows > (long long)img.coords * img.rows ||
       img.kblocks * 16 < img.K) {
     set_error("%s: rows or planes outside the plane image", name);
     return DISTIL_EINVAL;
@@ -270,12 +273,12 @@ inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long lo
   const long long threads = nrows * 32;
   Launch L(ctx, name, s);
   if (K > 2048 && K <= 4096)
-    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
+    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src, ROT><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
   else if (K > 1024 && K <= 2048)
-    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
+    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src, ROT><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
   else
-    split_rows_kernel<BF16, FIXED, NPC, Src><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, nrows, img, H,
-                                                                                                exps, norms);
+    split_rows_kernel<BF16, FIXED, NPC, Src, ROT><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, nrows, img,
+                                                                                                     H, exps, norms);
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
 }

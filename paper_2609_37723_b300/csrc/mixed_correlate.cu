@@ -691,13 +691,15 @@ static int gemm(distil_ctx* ctx, GemmSite site, const char* name, const PlaneImg
 // plane images, so that no pass needs more than two accumulator pairs and
 // the MMAs run 128 wide (three pairs fit TMEM only 80 wide, and 80-wide
 // MMAs take ~1.3x the time per column):
-//   pass A  the leading two pieces of each side (the first four planes):
-//           hi*hi | hi*mid + mid*hi, both pairs exact integer sums, stored
-//           by epi as D0 + D1;
+//   pass A  the leading two pieces of each side: hi*hi | hi*mid + mid*hi,
+//           both pairs exact integer sums, stored by epi as D0 + D1;
 //   pass B  the second-order terms hi*lo, mid*mid', lo*hi in one pair,
 //           added into the stored values in double-float by epi_add.
-// The classes accumulate exactly as with three pairs; D1 and D2 now meet in
-// double-float instead of FP32.
+// A holds the pieces hi, mid, lo (pass A reads its first four planes), B
+// the pieces in the order mid', lo, hi, mid, so that pass A reads B's last
+// four planes and pass B its first six: no pass copies a plane it does not
+// use.  The classes accumulate exactly as with three pairs; D1 and D2 now
+// meet in double-float instead of FP32.
 template <bool BF16, class EpiS, class EpiA>
 static int contract_two_pass(distil_ctx* ctx, GemmSite site, const char* name, const char* name_2nd,
                              const PlaneImg& A, const PlaneImg& B, tc::GemmCfg cfg, int batch, const EpiS& epi,
@@ -708,14 +710,14 @@ static int contract_two_pass(distil_ctx* ctx, GemmSite site, const char* name, c
     cfg.pa[p] = PA::pa[p];
     cfg.pb[p] = PA::pb[p];
   }
-  DISTIL_TRY((gemm<BF16, 4, 4, 2>(ctx, site, name, tc::first_planes(A, 4), tc::first_planes(B, 4), cfg, batch, epi, s)));
-  using PB = tc::SchemeProducts<6, 8, 1>;
+  DISTIL_TRY((gemm<BF16, 4, 4, 2>(ctx, site, name, tc::plane_view(A, 0, 4), tc::plane_view(B, 4, 4), cfg, batch, epi, s)));
+  using PB = tc::SchemeProducts<6, 6, 1>;
   cfg.nprod = PB::n;
   for (int p = 0; p < PB::n; ++p) {
     cfg.pa[p] = PB::pa[p];
     cfg.pb[p] = PB::pb[p];
   }
-  return gemm<BF16, 6, 8, 1>(ctx, site, name_2nd, A, B, cfg, batch, epi_add, s);
+  return gemm<BF16, 6, 6, 1>(ctx, site, name_2nd, A, tc::plane_view(B, 0, 6), cfg, batch, epi_add, s);
 }
 
 static inline unsigned nblk(long long work, int bs = 256) { return (unsigned)((work + bs - 1) / bs); }
@@ -727,8 +729,11 @@ static int split_tau_t(distil_ctx* ctx, const Scheme& sch, const float2* tau, co
   const long long n = nv;
   const int H = sch.H;
   DISTIL_TRY((split_rows<BF16, FIXED, NA>(ctx, "split_tau", AaSrc{tau, etau, nv}, 12 * n, w.Aa, H, w.eAa, s, w.nAa)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TTSrc{tau, etau, nv, w.nvp}, 4LL * w.nvp, w.TT, H, w.eTT, s)));
-  DISTIL_TRY((split_rows<BF16, FIXED, NB>(ctx, "split_tau", TcTSrc{TcSrc{tau, etau, nv}}, n, w.TcT, H, w.eTcT, s)));
+  // the B operands of the two-pass contractions (four pieces) in the piece
+  // order mid', lo, hi, mid (contract_two_pass)
+  constexpr int ROT = NB == 4 ? 2 : 0;
+  DISTIL_TRY((split_rows<BF16, FIXED, NB, TTSrc, ROT>(ctx, "split_tau", TTSrc{tau, etau, nv, w.nvp}, 4LL * w.nvp, w.TT, H, w.eTT, s)));
+  DISTIL_TRY((split_rows<BF16, FIXED, NB, TcTSrc, ROT>(ctx, "split_tau", TcTSrc{TcSrc{tau, etau, nv}}, n, w.TcT, H, w.eTcT, s)));
   return DISTIL_OK;
 }
 

@@ -43,15 +43,15 @@ namespace tc {
 // is rows rounded up to 8 plus 128, so any tile starting below `rows` can
 // be copied whole; rows past `rows` only reach outputs that are not kept.
 // Elements of the last K block past K must be zero (the writers store them).
-// An image stores ptot planes per (c, kb); a GEMM reads its first `planes`
-// (first_planes: the leading pieces only).
+// An image stores ptot planes per (c, kb); a GEMM reads `planes` of them
+// from plane p0 on (plane_view: a subset of the pieces).
 struct PlaneImg {
   void* base;
   long long rows, rows_pad;
-  int K, kblocks, planes, coords, ptot;
-  // first row of block (c, kb, p), in rows
+  int K, kblocks, planes, coords, ptot, p0;
+  // first row of block (c, kb, p), in rows (p counted from p0)
   __host__ __device__ __forceinline__ long long block(long long c, int kb, int p) const {
-    return ((c * kblocks + kb) * ptot + p) * rows_pad;
+    return ((c * kblocks + kb) * ptot + p0 + p) * rows_pad;
   }
   // element index of (c, p, r, k)
   __host__ __device__ __forceinline__ long long index(long long c, int p, long long r, int k) const {
@@ -72,11 +72,13 @@ inline PlaneImg plane_img(void* base, long long K, long long rows, long long coo
   g.planes = planes;
   g.coords = (int)coords;
   g.ptot = planes;
+  g.p0 = 0;
   return g;
 }
-// The same image read as its first np planes.
-inline PlaneImg first_planes(const PlaneImg& g, int np) {
+// The same image read as its planes p0 .. p0 + np - 1.
+inline PlaneImg plane_view(const PlaneImg& g, int p0, int np) {
   PlaneImg v = g;
+  v.p0 = g.p0 + p0;
   v.planes = np;
   return v;
 }
@@ -175,6 +177,14 @@ template <>
 struct SchemeProducts<6, 8, 1> {
   static constexpr int n = 3;
   static constexpr int pa[3] = {0, 1, 2}, pb[3] = {3, 2, 0}, acc[3] = {0, 0, 0};
+};
+// the same, with the B operand viewed as the pieces [mid', lo, hi] (the
+// first six planes of a B image stored in the piece order mid', lo, hi, mid,
+// whose last four planes are the [hi, mid] of the first pass)
+template <>
+struct SchemeProducts<6, 6, 1> {
+  static constexpr int n = 3;
+  static constexpr int pa[3] = {0, 1, 2}, pb[3] = {1, 0, 2}, acc[3] = {0, 0, 0};
 };
 template <>
 struct SchemeProducts<8, 8, 1> {

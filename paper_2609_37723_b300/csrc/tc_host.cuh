@@ -20,8 +20,8 @@ inline bool images_fit(const char* name, const PlaneImg& A, const PlaneImg& B, c
     const long long top = (q < m.bmod - 1 ? q : m.bmod - 1);
     return top * m.bmul + m.badd;
   };
-  bool ok = A.planes == npla && B.planes == nplb && A.planes <= A.ptot && B.planes <= B.ptot && kb <= A.kblocks &&
-            kb <= B.kblocks;
+  bool ok = A.planes == npla && B.planes == nplb && A.p0 >= 0 && B.p0 >= 0 && A.p0 + A.planes <= A.ptot &&
+            B.p0 + B.planes <= B.ptot && kb <= A.kblocks && kb <= B.kblocks;
   ok = ok && cfg.a.bdiv > 0 && cfg.a.bmod > 0 && cfg.b.bdiv > 0 && cfg.b.bmod > 0 && cfg.a.bmul >= 0 &&
        cfg.b.bmul >= 0 && cfg.a.badd >= 0 && cfg.b.badd >= 0;
   ok = ok && coord_max(cfg.a) < A.coords && coord_max(cfg.b) < B.coords;
