@@ -307,6 +307,12 @@ struct ColMap {
   __device__ __forceinline__ bool keep(int c) const { return !cdiv || (c % cdiv) < cvalid; }
 };
 
+// 16-byte load of a complex double-float (p 16-byte aligned)
+__device__ __forceinline__ CDF ld_cdf(const CDF* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return cdf_make(df_make(v.x, v.y), df_make(v.z, v.w));
+}
+
 // The GEMM hands the epilogue each value as an unevaluated FP32 pair
 // (leading-slice part, cross-term part): D = re0 + re1, im0 + im1.
 
@@ -358,13 +364,19 @@ struct EpiAddCDF : tc::EpiStateless {
   __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     CDF* base = out + (long long)(batch / b_lo) * sb_hi + (long long)(batch % b_lo) * sb_lo + (long long)row * sr;
+    // all 16 loads in flight before the first store (the stores could
+    // otherwise alias the later loads and serialise the round trips)
+    CDF old[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int c = col0 + e;
-      if (c >= N) break;
-      if (!cm.keep(c)) continue;
-      CDF* d = base + cm(c);
-      *d = cdf_add(*d, cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e])));
+      old[e] = (c < N && cm.keep(c)) ? ld_cdf(base + cm(c)) : cdf_zero();
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int c = col0 + e;
+      if (c < N && cm.keep(c))
+        base[cm(c)] = cdf_add(old[e], cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e])));
     }
   }
 };

@@ -124,11 +124,18 @@ struct EpiPhiAcc : tc::EpiStateless {
   __device__ __forceinline__ void operator()(State&, int, int row, int col0, const float* re0, const float* re1,
                                              const float* im0, const float* im1) const {
     CDF* dst = acc + (long long)col0 * P2 + row;
+    // all 16 loads in flight before the first store (the stores could
+    // otherwise alias the later loads and serialise the round trips)
+    CDF old[16];
+    if (!first) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) old[e] = col0 + e < N ? ld_cdf(dst + e * P2) : cdf_zero();
+    }
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       if (col0 + e >= N) break;
       CDF v = cdf_make(two_sum(re0[e], re1[e]), two_sum(im0[e], im1[e]));
-      if (!first) v = cdf_add(v, dst[e * P2]);
+      if (!first) v = cdf_add(v, old[e]);
       dst[e * P2] = v;
     }
   }
