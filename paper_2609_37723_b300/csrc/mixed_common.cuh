@@ -150,20 +150,24 @@ __device__ __forceinline__ void make_pieces(DF x, Pow2 s, typename tc::Piece<BF1
 // two-pass contractions).  Lanes with consecutive k fill whole 32-byte rows
 // of a K block together.
 template <bool BF16, bool FIXED, int NPC, int ROT = 0>
-__device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long c, long long rr, int k, const CDF& v,
-                                             Pow2 sc) {
+__device__ __forceinline__ void store_pieces_at(typename tc::Piece<BF16>::T* out, long long ps, const CDF& v, Pow2 sc) {
   using P16 = typename tc::Piece<BF16>::T;
   P16 pr[NPC], pi[NPC];
   make_pieces<BF16, FIXED, NPC>(v.re, sc, pr);
   make_pieces<BF16, FIXED, NPC>(v.im, sc, pi);
-  P16* out = reinterpret_cast<P16*>(img.base) + img.index(c, 0, rr, k);
-  const long long ps = img.rows_pad * 16;  // plane stride in elements
 #pragma unroll
   for (int i = 0; i < NPC; ++i) {
     const int slot = (i + ROT) % NPC;
     out[(2 * slot) * ps] = pr[i];
     out[(2 * slot + 1) * ps] = pi[i];
   }
+}
+template <bool BF16, bool FIXED, int NPC, int ROT = 0>
+__device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long c, long long rr, int k, const CDF& v,
+                                             Pow2 sc) {
+  using P16 = typename tc::Piece<BF16>::T;
+  store_pieces_at<BF16, FIXED, NPC, ROT>(reinterpret_cast<P16*>(img.base) + img.index(c, 0, rr, k), img.rows_pad * 16,
+                                         v, sc);
 }
 
 // Split rows of a complex operand into 2*NPC planes with a per-row exponent.
@@ -199,8 +203,13 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   }
   const Pow2 sc = pow2_pair(H - e);
   const long long coord = r / img.rows, rr = r % img.rows;
-  for (int k = lane; k < Kp; k += 32)
-    store_pieces<BF16, FIXED, NPC, ROT>(img, coord, rr, k, k < K ? src(r, k) : cdf_zero(), sc);
+  // k = lane + 32 u: each step moves two K blocks on; the swizzle half and
+  // k & 7 stay those of the lane
+  using P16 = typename tc::Piece<BF16>::T;
+  P16* out = reinterpret_cast<P16*>(img.base) + img.index(coord, 0, rr, lane);
+  const long long ps = img.rows_pad * 16, step = 2 * (long long)img.ptot * ps;
+  for (int k = lane; k < Kp; k += 32, out += step)
+    store_pieces_at<BF16, FIXED, NPC, ROT>(out, ps, k < K ? src(r, k) : cdf_zero(), sc);
 }
 
 // Long rows (K <= 512 PER): one block of 512 threads per row, each thread
@@ -238,11 +247,16 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::Pla
   __syncthreads();
   const Pow2 sc = pow2_pair(H - sh_e);
   const long long coord = r / img.rows, rr = r % img.rows;
+  // k = tid + 512 u: each step moves 32 K blocks on; the swizzle half and
+  // k & 7 stay those of the thread
+  using P16 = typename tc::Piece<BF16>::T;
+  P16* out = reinterpret_cast<P16*>(img.base) + img.index(coord, 0, rr, threadIdx.x);
+  const long long ps = img.rows_pad * 16, step = 32 * (long long)img.ptot * ps;
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int k = threadIdx.x + 512 * u;
     if (k >= Kp) break;
-    store_pieces<BF16, FIXED, NPC, ROT>(img, coord, rr, k, v[u], sc);
+    store_pieces_at<BF16, FIXED, NPC, ROT>(out + u * step, ps, v[u], sc);
   }
 }
 

@@ -227,9 +227,22 @@ struct EpiSplitU : tc::EpiStateless {
   PlaneImg out;
   const int* eU;
   int n, H;
+  // the exponent of U row (row, k) for the k of the warp's first slice,
+  // loaded before the accumulator wait (at N_v >= 128 one 128-wide tile
+  // has a single k)
+  struct State {
+    int k, e;
+  };
+  __device__ __forceinline__ void prefetch(State& st, int batch, int row, int col) const {
+    const long long n2 = (long long)n * n;
+    st.k = col / n;
+    st.e = (row < n && col < n2) ? eU[(long long)(batch >> 2) * n2 + (long long)row * n + st.k] : 0;
+  }
+  __device__ __forceinline__ void begin(State&) const {}
+  __device__ __forceinline__ void end(State&, int) const {}
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
-  __device__ __forceinline__ void operator()(State&, int batch, int row, int col0, const float* re0, const float* re1,
-                                             const float* im0, const float* im1) const {
+  __device__ __forceinline__ void operator()(State& st, int batch, int row, int col0, const float* re0,
+                                             const float* re1, const float* im0, const float* im1) const {
     using P16 = typename tc::Piece<BF16>::T;
     const long long n2 = (long long)n * n;
     const int aa = batch >> 2, beta = batch & 3;  // aa = a*3 + a'
@@ -241,7 +254,8 @@ struct EpiSplitU : tc::EpiStateless {
       // with one 32-byte store
       const int k = col0 / n, j0 = col0 % n;
       const long long ur = (long long)row * n + k;
-      const Pow2 sc = pow2_pair(H - eU[(long long)aa * n2 + ur]);
+      const int eu = k == st.k ? st.e : eU[(long long)aa * n2 + ur];
+      const Pow2 sc = pow2_pair(H - eu);
       const int sw = (int)(ur >> 2) & 1;  // halves swapped in this row
       uint32_t w[2 * NPC][8];
 #pragma unroll

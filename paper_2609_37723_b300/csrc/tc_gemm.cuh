@@ -250,6 +250,9 @@ struct MmaSchedule {
 // derive from this.
 struct EpiStateless {
   struct State {};
+  // before the accumulator is waited for: loads the tile's slices will use
+  // (row, first column of the warp's first slice)
+  __device__ __forceinline__ void prefetch(State&, int, int, int) const {}
   __device__ __forceinline__ void begin(State&) const {}
   __device__ __forceinline__ void end(State&, int) const {}
 };
@@ -473,11 +476,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int row = m_tile * 128 + q * 32 + lane;
     int ea, ebp[2];
     tile_exps<NT>(cfg, ca, cb, row, n_tile, half, lane, ea, ebp);
+    typename Epi::State st;
+    epi.prefetch(st, batch, row, n_tile * NT + half * 16);
     bool ok = mbar_wait(accf, 0, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
     ok = __all_sync(0xffffffffu, ok && !*(volatile uint32_t*)abort_flag);  // warp-uniform for tcgen05.ld
     tc_fence_after();
     if (ok) {
-      typename Epi::State st;
       epi.begin(st);
       const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
@@ -657,6 +661,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int row = m_tile * 128 + q * 32 + lane;
       int ea, ebp[2];
       tile_exps<NT>(cfg, ca, cb, row, n_tile, half, lane, ea, ebp);
+      typename Epi::State st;
+      epi.prefetch(st, batch, row, n_tile * NT + half * 16);
       bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
       ok = __all_sync(0xffffffffu, ok && !*abort_v);  // warp-uniform for tcgen05.ld
       if (!ok) {
@@ -664,7 +670,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      typename Epi::State st;
       epi.begin(st);
       const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
@@ -868,6 +873,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int row = m_tile * 128 + q * 32 + lane;
       int ea, ebp[2];
       tile_exps<NT>(cfg, ca, cb, row, n_tile, half, lane, ea, ebp);
+      typename Epi::State st;
+      epi.prefetch(st, batch, row, n_tile * NT + half * 16);
       bool ok = mbar_wait(&tfull[buf], use & 1, cfg.err, TC_ERR_ACC_WAIT, cfg.wait);
       ok = __all_sync(0xffffffffu, ok && !*abort_v);
       if (!ok) {
@@ -875,7 +882,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      typename Epi::State st;
       epi.begin(st);
       const uint32_t tl = tmem + buf * SET + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
