@@ -985,11 +985,11 @@ def kernel_cmacs(name, p):
 # capture of the kernels as they stand: (workload, mode, kernel) -> bytes.
 # The L48_Nt96_Nv256 elementals launch is too large to capture with
 # --set full; its figure is the L32_Nv128 one-timeslice capture of the
-# bulk-copy kernel (538.9 MB read, 3.2 MB written,
+# bulk-copy kernel (539.3 MB read, 3.3 MB written,
 # profiles/tc_gemm_L32_Nv128_one_timeslice.md) scaled by the operand units
 # of a launch, (pairs + (i, p) rows) x K chunk: x 4.23.
 TRAFFIC = {
-    ("L48_Nt96_Nv256", "fp16x6", "tc_gemm_elementals"): 542.1e6 * (32640 + 2304) / (8128 + 128),
+    ("L48_Nt96_Nv256", "fp16x6", "tc_gemm_elementals"): 542.6e6 * (32640 + 2304) / (8128 + 128),
 }
 
 
