@@ -32,6 +32,8 @@
 //    l = fp16(t - h); accumulation rounding is not exact.
 #pragma once
 #include <cuda_bf16.h>
+#include <type_traits>
+#include <utility>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -170,6 +172,29 @@ __device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long 
                                          v, sc);
 }
 
+// A source may bind a row once (Src::row(r), returning an object with
+// operator()(k) and approx(k)) so that the per-row part of its indexing
+// runs once per row instead of once per element; otherwise bind_row wraps
+// Src::operator()(r, k).
+template <class S, class = void>
+struct has_row : std::false_type {};
+template <class S>
+struct has_row<S, std::void_t<decltype(std::declval<const S&>().row(0LL))>> : std::true_type {};
+template <class Src>
+struct RowOf {
+  const Src* src;
+  long long r;
+  __device__ __forceinline__ CDF operator()(int k) const { return (*src)(r, k); }
+  __device__ __forceinline__ float2 approx(int k) const { return src->approx(r, k); }
+};
+template <class Src>
+__device__ __forceinline__ auto bind_row(const Src& src, long long r) {
+  if constexpr (has_row<Src>::value)
+    return src.row(r);
+  else
+    return RowOf<Src>{&src, r};
+}
+
 // Split rows of a complex operand into 2*NPC planes with a per-row exponent.
 // Global row r = coord * img.rows + rr goes to plane image img (tc_gemm.cuh:
 // PlaneImg; plane 2 i + re/im holds piece i) at coordinate coord, row rr,
@@ -185,9 +210,10 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   const int lane = threadIdx.x & 31;
   if (r >= nrows) return;
   const int K = img.K, Kp = img.kblocks * 16;
+  const auto row = bind_row(src, r);
   float m = 0.f, ss = 0.f;
   for (int k = lane; k < K; k += 32) {
-    const float2 v = src.approx(r, k);  // FP32 estimate: enough for the exponent and the norm
+    const float2 v = row.approx(k);  // FP32 estimate: enough for the exponent and the norm
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
     ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
   }
@@ -209,7 +235,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
   P16* out = reinterpret_cast<P16*>(img.base) + img.index(coord, 0, rr, lane);
   const long long ps = img.rows_pad * 16, step = 2 * (long long)img.ptot * ps;
   for (int k = lane; k < Kp; k += 32, out += step)
-    store_pieces_at<BF16, FIXED, NPC, ROT>(out, ps, k < K ? src(r, k) : cdf_zero(), sc);
+    store_pieces_at<BF16, FIXED, NPC, ROT>(out, ps, k < K ? row(k) : cdf_zero(), sc);
 }
 
 // Long rows (K <= 512 PER): one block of 512 threads per row, each thread
@@ -223,12 +249,13 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::Pla
   const long long r = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int K = img.K, Kp = img.kblocks * 16;
+  const auto row = bind_row(src, r);
   CDF v[PER];
   float m = 0.f, ss = 0.f;
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int k = threadIdx.x + 512 * u;
-    v[u] = k < K ? src(r, k) : cdf_zero();
+    v[u] = k < K ? row(k) : cdf_zero();
     m = fmaxf(m, fmaxf(fabsf(v[u].re.hi), fabsf(v[u].im.hi)));
     ss = fmaf(v[u].re.hi, v[u].re.hi, fmaf(v[u].im.hi, v[u].im.hi, ss));
   }
