@@ -172,6 +172,36 @@ __device__ __forceinline__ void store_pieces(const tc::PlaneImg& img, long long 
                                          v, sc);
 }
 
+// Two 16-bit values packed as one 32-bit word (a in the low half).
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+// The three fixed-point pieces (hi, mid, lo 2^-W) of two double-floats x0,
+// x1 scaled by one power of two s in FP32's normal range, as packed pairs:
+// the values make_pieces<BF16, true, 3> gives with pow2_pair scaling (the
+// power-of-two products are exact either way), converted two at a time.
+template <bool BF16>
+__device__ __forceinline__ void pieces3_pair(DF x0, DF x1, float s, uint32_t& w_hi, uint32_t& w_mid, uint32_t& w_lo) {
+  constexpr int W = SliceBits<BF16>::W;
+  constexpr float sw = (float)(1 << W), isw = 1.f / (float)(1 << W);
+  const float th0 = x0.hi * s, tl0 = x0.lo * s, th1 = x1.hi * s, tl1 = x1.lo * s;
+  const float hi0 = rintf(th0), hi1 = rintf(th1);
+  const float r0 = __fmul_rn(__fadd_rn(__fsub_rn(th0, hi0), tl0), sw);
+  const float r1 = __fmul_rn(__fadd_rn(__fsub_rn(th1, hi1), tl1), sw);
+  const float mid0 = rintf(r0), mid1 = rintf(r1);
+  const float lo0 = rintf(__fmul_rn(__fsub_rn(r0, mid0), sw)), lo1 = rintf(__fmul_rn(__fsub_rn(r1, mid1), sw));
+  w_hi = pack2<BF16>(hi0, hi1);
+  w_mid = pack2<BF16>(mid0, mid1);
+  w_lo = pack2<BF16>(lo0 * isw, lo1 * isw);
+}
+
 // A source may bind a row once (Src::row(r), returning an object with
 // operator()(k) and approx(k)) so that the per-row part of its indexing
 // runs once per row instead of once per element; otherwise bind_row wraps

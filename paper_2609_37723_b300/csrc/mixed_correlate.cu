@@ -241,6 +241,24 @@ struct EpiSplitU : tc::EpiStateless {
   __device__ __forceinline__ void begin(State&) const {}
   __device__ __forceinline__ void end(State&, int) const {}
   __device__ __forceinline__ bool skip_tile(int, int, int) const { return false; }
+  // the 2 NPC plane rows of U row ur from K element kk0 (a K block's first):
+  // one 32-byte store each, halves in the row's swizzled order
+  template <class P16>
+  __device__ __forceinline__ void store_row(P16* o, long long ur, int aa, int kk0, int sw,
+                                            const uint32_t (&w)[2 * NPC][8]) const {
+    P16* d = o + ((out.block(aa, kk0 >> 4, 0) + ur) << 4);
+    const long long ps = out.rows_pad * 16;
+#pragma unroll
+    for (int pl = 0; pl < 2 * NPC; ++pl) {
+      uint32_t v[8];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        v[x] = sw ? w[pl][4 + x] : w[pl][x];
+        v[4 + x] = sw ? w[pl][x] : w[pl][4 + x];
+      }
+      tc::st_global_32B(d + pl * ps, v);
+    }
+  }
   __device__ __forceinline__ void operator()(State& st, int batch, int row, int col0, const float* re0,
                                              const float* re1, const float* im0, const float* im1) const {
     using P16 = typename tc::Piece<BF16>::T;
@@ -258,6 +276,21 @@ struct EpiSplitU : tc::EpiStateless {
       const Pow2 sc = pow2_pair(H - eu);
       const int sw = (int)(ur >> 2) & 1;  // halves swapped in this row
       uint32_t w[2 * NPC][8];
+      if constexpr (FIXED && NPC == 3) {
+        if (H - eu >= -126 && H - eu <= 127) {
+          // one exact scaling per value, conversions two at a time
+          const float s1 = tc::pow2f(H - eu);
+#pragma unroll
+          for (int e = 0; e < 16; e += 2) {
+            pieces3_pair<BF16>(two_sum(re0[e], re1[e]), two_sum(re0[e + 1], re1[e + 1]), s1, w[0][e / 2],
+                               w[2][e / 2], w[4][e / 2]);
+            pieces3_pair<BF16>(two_sum(im0[e], im1[e]), two_sum(im0[e + 1], im1[e + 1]), s1, w[1][e / 2],
+                               w[3][e / 2], w[5][e / 2]);
+          }
+          store_row(o, ur, aa, beta * n + j0, sw, w);
+          return;
+        }
+      }
 #pragma unroll
       for (int e = 0; e < 16; e += 2) {
         P16 pr0[NPC], pi0[NPC], pr1[NPC], pi1[NPC];
@@ -273,20 +306,7 @@ struct EpiSplitU : tc::EpiStateless {
                                 ((uint32_t)reinterpret_cast<const uint16_t&>(pi1[q]) << 16);
         }
       }
-      // the row's first element: index of K element beta n + j0 with the
-      // half-swap undone (j0 is a multiple of 16)
-      P16* d = o + ((out.block(aa, (beta * n + j0) >> 4, 0) + ur) << 4);
-      const long long ps = out.rows_pad * 16;
-#pragma unroll
-      for (int pl = 0; pl < 2 * NPC; ++pl) {
-        uint32_t v[8];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          v[x] = sw ? w[pl][4 + x] : w[pl][x];
-          v[4 + x] = sw ? w[pl][x] : w[pl][4 + x];
-        }
-        tc::st_global_32B(d + pl * ps, v);
-      }
+      store_row(o, ur, aa, beta * n + j0, sw, w);
       return;
     }
 #pragma unroll
