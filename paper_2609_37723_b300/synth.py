@@ -22,7 +22,12 @@ Conventions (all fixed here, used by every consumer):
 
 Random streams: numpy PCG64 seeded by SeedSequence(2609, spawn_key=(config,
 cfg, t, field)) with field 0 = eigenvectors, 1 = perambulator, 2 = N_v draw,
-3 = Laplacian eigenvalues.
+3 = Laplacian eigenvalues, 4 = gauge links.
+
+Meson workloads (Sec. 4 of the paper, "Improved charmonium operators") add
+spatial gauge links U[t][k][s][a][b] (direction k = x, y, z; row a, column
+b), each an SU(3) matrix drawn from the Haar measure; the covariant
+derivatives of the meson operators read them.
 """
 from __future__ import annotations
 
@@ -34,7 +39,7 @@ import numpy as np
 from scipy.linalg import solve_triangular
 
 BASE_SEED = 2609
-FIELD_V, FIELD_TAU, FIELD_NV, FIELD_LAMBDA = 0, 1, 2, 3
+FIELD_V, FIELD_TAU, FIELD_NV, FIELD_LAMBDA, FIELD_U = 0, 1, 2, 3, 4
 
 
 def rng_for(config: int, cfg: int, t: int, field: int) -> np.random.Generator:
@@ -63,6 +68,19 @@ def orthonormal_columns(a: np.ndarray) -> np.ndarray:
         r = np.linalg.cholesky(g).conj().T  # upper triangular, g = r^H r
         q = solve_triangular(r, q.T, trans="T", lower=False).T  # q r^{-1}
     return q
+
+
+def haar_su3(rng: np.random.Generator, shape) -> np.ndarray:
+    """Haar-distributed SU(3) matrices [*shape][3][3]: QR of a complex
+    Gaussian with the phases of R's diagonal moved into Q (Mezzadri's
+    recipe for the Haar measure on U(3)), then the determinant's phase
+    divided out by a third of it on every entry."""
+    z = complex_gaussian(rng, tuple(shape) + (3, 3))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    q = q * (d / np.abs(d))[..., None, :]
+    det = np.linalg.det(q)
+    return q * np.exp(-1j * np.angle(det) / 3.0)[..., None, None]
 
 
 @dataclasses.dataclass
@@ -117,6 +135,15 @@ class Problem:
         i = np.arange(self.nv, dtype=np.float64)
         lam = 0.05 * (i + 1.0) ** (2.0 / 3.0) * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, self.nv))
         return np.sort(lam)
+
+    def links(self, t: int) -> np.ndarray:
+        """U[t]: [3][V3][3][3] spatial gauge links, Haar-random SU(3)."""
+        rng = rng_for(self.config_id, self.cfg, t, FIELD_U)
+        return haar_su3(rng, (3, self.V3)).astype(self.dtype)
+
+    def all_links(self, ts: Optional[Sequence[int]] = None) -> np.ndarray:
+        ts = range(self.nt) if ts is None else ts
+        return np.stack([self.links(t) for t in ts])
 
     def all_eigvecs(self, ts: Optional[Sequence[int]] = None) -> np.ndarray:
         ts = range(self.nt) if ts is None else ts
@@ -181,3 +208,41 @@ def small(L: int, nt: int, nv: int, mom=MOM_C1, sigmas=(0.3, 0.6, 1.0), decay=0.
     """Small problems for tests (config id 0, cfg = seed_cfg)."""
     return Problem(f"L{L}_Nt{nt}_Nv{nv}", L, nt, nv, _mom(mom),
                    gaussian_profiles(nv, sigmas), decay, np.dtype(dtype), 0, seed_cfg)
+
+
+@dataclasses.dataclass
+class MesonProblem:
+    """One meson workload: a distillation problem (eigenvectors, links,
+    perambulators, momenta, N_B Gaussian profiles per Gamma) plus the size
+    of the pruned matrix and the time separation of the pruning SVD."""
+    base: Problem
+    nkeep: int
+    t_prune: int
+
+    def __getattr__(self, name):
+        return getattr(self.base, name)
+
+
+def meson_config(which: str, cfg: int = 0) -> MesonProblem:
+    """Meson workloads shaped like the charmonium study (Sec. 4: N_f = 2,
+    24^3 x 48, N_v = 200, seven Gaussian profiles for each of three Gammas
+    giving a 21 x 21 matrix pruned to 8 x 8):
+      "charm"  L = 24, N_t = 48, N_v = 200, p = 0, perambulators complex64
+               decaying like exp(-0.5 t), profile widths 0.15 .. 1.2
+      "small"  L = 8, N_t = 6, N_v = 24, momenta 0 and (0, 0, 1), complex64
+      "tiny"   L = 4, N_t = 4, N_v = 6, momenta 0 and (0, 0, 1), complex128
+    """
+    sig = [0.15 * 8.0 ** (a / 6.0) for a in range(7)]
+    if which == "charm":
+        base = Problem("L24_Nt48_Nv200_meson", 24, 48, 200, _mom([(0, 0, 0)]),
+                       gaussian_profiles(200, sig), 0.5, np.dtype(np.complex64), 6, cfg)
+        return MesonProblem(base, 8, 2)
+    if which == "small":
+        base = Problem("L8_Nt6_Nv24_meson", 8, 6, 24, _mom([(0, 0, 0), (0, 0, 1)]),
+                       gaussian_profiles(24, sig), 0.5, np.dtype(np.complex64), 7, cfg)
+        return MesonProblem(base, 8, 2)
+    if which == "tiny":
+        base = Problem("L4_Nt4_Nv6_meson", 4, 4, 6, _mom([(0, 0, 0), (0, 0, 1)]),
+                       gaussian_profiles(6, sig), 0.5, np.dtype(np.complex128), 8, cfg)
+        return MesonProblem(base, 8, 1)
+    raise ValueError(f"unknown meson workload {which}")
