@@ -12,6 +12,9 @@ plain FP32/FP64 CUDA-core paths are reported beside it.
                     [--impl ours|reference] [--ncfg K] [--nt NT]
                     [--no-cpu-baseline] [--no-parity] [--no-plain]
 
+--meson charm times the one-meson path instead (L=24, N_t=48, N_v=200,
+3 Gammas x 7 profiles, pruned to 8 x 8): one step = one configuration.
+
 Default: workload 5 (L=48, N_t=96, N_v=256, 9 momenta, 8 profiles), mode
 fp16x6, one step = one sink timeslice of it (elementals of every momentum,
 C_ab(t) for every (p, a, b), the GEVP of C(t) with eigenvectors), 3 warm-up
@@ -1105,6 +1108,264 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# --------------------------------------------------------------------------- mesons
+
+MESON_METRIC = "meson C_ab(t) entries/s"
+
+
+def _meson_eig_worker(args):
+    which, cfg, jobs, shm_name, shape, dtype = args
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=shm_name)
+    out = np.ndarray(shape, dtype=dtype, buffer=shm.buf)
+    m = synth.meson_config(which, cfg)
+    for slot, t in jobs:
+        out[slot] = m.eigvecs(t)
+    del out
+    shm.close()
+    return len(jobs)
+
+
+def meson_inputs(which: str, cfg: int, workers: int):
+    """Host inputs of one meson configuration: v, U, tau (numpy, the bytes the
+    tests draw); the eigenvectors in parallel spawned processes."""
+    m = synth.meson_config(which, cfg)
+    shape = (m.nt, m.nv, m.V3, 3)
+    dtype = np.dtype(m.dtype)
+    if workers > 1 and m.nt > 1:
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        shm = shared_memory.SharedMemory(create=True, size=int(np.prod(shape)) * dtype.itemsize)
+        try:
+            jobs = list(enumerate(range(m.nt)))
+            chunks = [jobs[w::workers] for w in range(workers)]
+            with mp.get_context("spawn").Pool(workers) as pool:
+                pool.map(_meson_eig_worker, [(which, cfg, c, shm.name, shape, dtype.str) for c in chunks if c])
+            v = np.array(np.ndarray(shape, dtype=dtype, buffer=shm.buf))
+        finally:
+            shm.close()
+            shm.unlink()
+    else:
+        v = m.all_eigvecs()
+    return m, v, m.all_links(), m.all_perambulators()
+
+
+def meson_cmacs(name, m):
+    """Complex MACs one configuration asks of each meson contraction family."""
+    n, nops, V3 = m.nv, 3 * m.nb, m.V3
+    table = {
+        "tc_gemm_meson_elem": (7.0 * n * m.np_ * n * 3 * V3 * m.nt,
+                               "7 N_p N_v^2 3 V3 per timeslice: all displacements d, all (i, j)"),
+        "tc_gemm_meson_q": (nops * 64.0 * n ** 3 * m.np_ * m.nt,
+                            "3 N_B (4 N_v)^3 per (t, p): Q_b = Phibar_b g5 tau^dagger g5, dense spin-mode"),
+        "tc_gemm_meson_x": (nops * 64.0 * n ** 3 * m.np_ * m.nt, "3 N_B (4 N_v)^3 per (t, p): X_b = tau Q_b"),
+    }
+    return table.get(name)
+
+
+def meson_split_products(name) -> int:
+    return 8 if name == "tc_gemm_meson_elem" else 6
+
+
+def meson_bytes(name, m):
+    """Algorithmic HBM bytes per configuration of the memory-side families."""
+    n, nops, V3, nt = m.nv, 3 * m.nb, m.V3, m.nt
+    table = {
+        "meson_nabla": ((8.0 * n * 3 * V3 + 3 * 72.0 * V3 + 3 * 16.0 * n * 3 * V3) * nt,
+                        "v (8 B) and the links read, three nabla fields (16 B) written, per t"),
+        "meson_reduce": (16.0 * nops * 16 * n * n * m.np_ * nt, "X (3 N_B (4 N_v)^2 x 16 B) read per (t, p)"),
+    }
+    return table.get(name)
+
+
+def meson_rooflines(kstats, m, pk, steps):
+    tpeak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
+    hpeak = pk.get("hbm_gbs") or 6400.0
+    out = []
+    for name, (launches, ms) in sorted(kstats.items(), key=lambda kv: -kv[1][1]):
+        if ms <= 0:
+            continue
+        c = meson_cmacs(name, m)
+        if c is not None:
+            ach = 8.0 * meson_split_products(name) * c[0] * steps / (ms / 1e3) / 1e12
+            out.append({"kernel": name, "bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
+                        "frac": ach / tpeak, "ms_per_step": ms / steps, "launches": launches,
+                        "per_unit": c[1], "split_products": meson_split_products(name)})
+            continue
+        b = meson_bytes(name, m)
+        if b is not None:
+            ach = b[0] * steps / (ms / 1e3) / 1e9
+            out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hpeak, "unit": "GB/s",
+                        "frac": ach / hpeak, "ms_per_step": ms / steps, "launches": launches, "per_unit": b[1]})
+    return out
+
+
+def meson_cpu_baseline(m, v, U, tau, t: int = 1):
+    """The meson oracle, as it stands, on one sink timeslice of the workload:
+    its elementals and its C_ab(t) (the t = 0 source elementals computed
+    first, untimed: they serve every timeslice).  Returns the baseline entry
+    and the oracle's C(t) for a parity check of that column."""
+    from oracle import meson as om
+    src = om.elementals_t(v[0].astype(np.complex128), U[0].astype(np.complex128), m.L, m.mom)
+    t0 = time.perf_counter()
+    phi = om.elementals_t(v[t].astype(np.complex128), U[t].astype(np.complex128), m.L, m.mom)
+    t1 = time.perf_counter()
+    C = om.correlator_t(phi, src, tau[t].astype(np.complex128), m.prof)
+    t2 = time.perf_counter()
+    entries = m.np_ * (3 * m.nb) ** 2
+    return ({"value": entries / (t2 - t0), "unit": MESON_METRIC, "cores": OracleSlices.cores(), "kind": "oracle",
+             "sample": f"one sink timeslice (t = {t}) of {m.nt}: elementals {t1 - t0:.1f} s + C_ab(t) "
+                       f"{t2 - t1:.1f} s, numpy FP64 with BLAS threads (source elementals untimed)",
+             "seconds": t2 - t0}, C)
+
+
+def run_meson(args):
+    """One step = one whole meson configuration (default L = 24, N_t = 48,
+    N_v = 200, p = 0, 3 Gammas x 7 profiles): the elementals of every
+    timeslice and displacement, the 21 x 21 C_ab(t) for every t, the pruning
+    to 8 x 8 at t_p and the GEVP of the pruned matrix.  With N ranks rank r
+    runs configuration r (weak scaling, no collective on the data path)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    which = args.meson
+    workers = min(32, os.cpu_count() or 1)
+    log(f"generating meson workload {which}, configuration {rank}")
+    m, v_h, U_h, tau_h = meson_inputs(which, rank, workers)   # before any CUDA call
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2609_37723_b300 import distil
+    v_pin = torch.from_numpy(np.ascontiguousarray(v_h.astype(np.complex64))).pin_memory()
+    U_pin = torch.from_numpy(np.ascontiguousarray(U_h.astype(np.complex64))).pin_memory()
+    tau_pin = torch.from_numpy(np.ascontiguousarray(tau_h.astype(np.complex64))).pin_memory()
+    v, U, tau = v_pin.to(dev), U_pin.to(dev), tau_pin.to(dev)
+    prof = torch.from_numpy(np.ascontiguousarray(m.prof)).to(dev)
+    nops = 3 * m.nb
+    phi = torch.empty((m.nt, m.np_, 7, m.nv, m.nv), dtype=torch.complex128, device=dev)
+    C = torch.empty((m.np_, nops, nops, m.nt), dtype=torch.complex128, device=dev)
+    ws_e = torch.empty(distil.meson_elementals_workspace(m.L, m.nt, m.nv, m.np_), dtype=torch.uint8, device=dev)
+    ws_c = torch.empty(distil.meson_correlate_workspace(m.nv, m.np_, m.nb), dtype=torch.uint8, device=dev)
+    t0_gevp = 1
+    stream = torch.cuda.current_stream()
+    log(f"device: v {v.numel() * 8 / 1e9:.2f} GB, workspaces {ws_e.numel() / 1e9:.2f} + {ws_c.numel() / 1e9:.2f} GB")
+    res = {}
+
+    def step(vv, UU, tt):
+        distil.meson_elementals(vv, UU, m.L, m.mom, out=phi, workspace=ws_e)
+        distil.meson_correlate(phi, phi[0], tt, prof, out=C, workspace=ws_c)
+        Ct, Un, sv = distil.meson_prune(C, m.t_prune, m.nkeep)
+        res["lam"] = distil.gevp(Ct, t0_gevp)
+        res["sv"] = sv
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        step(v, U, tau)
+        torch.cuda.synchronize()
+        log(f"warm-up step {i} done")
+    distil.profile_enable(timing=True, device=local)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        step(v, U, tau)
+    torch.cuda.nvtx.range_pop()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kstats = distil.profile_read(device=local)
+    distil.profile_enable(timing=False, device=local)
+    entries = m.np_ * nops * nops * m.nt
+    value, _, ms_max = job_throughput(entries, ms, args.steps, dist if world > 1 else None, dev)
+    ms_step = ms_max / args.steps
+    log(f"timed region: {ms_step:.1f} ms per configuration")
+
+    # end to end: host v, U, tau in and C, lambda out every step, through the same calls
+    e2e_steps = max(1, min(args.steps, 2))
+    v_in, U_in, tau_in = torch.empty_like(v), torch.empty_like(U), torch.empty_like(tau)
+    C_host = torch.empty(C.shape, dtype=C.dtype).pin_memory()
+    lam_host = torch.empty(res["lam"].shape, dtype=res["lam"].dtype).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        v_in.copy_(v_pin, non_blocking=True)
+        U_in.copy_(U_pin, non_blocking=True)
+        tau_in.copy_(tau_pin, non_blocking=True)
+        step(v_in, U_in, tau_in)
+        C_host.copy_(C, non_blocking=True)
+        lam_host.copy_(res["lam"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_value, _, _ = job_throughput(entries, e0.elapsed_time(e1), e2e_steps, dist if world > 1 else None, dev)
+    h2d = sum(x.numel() * x.element_size() for x in (v_pin, U_pin, tau_pin))
+    d2h = C_host.numel() * 16 + lam_host.numel() * 16
+    out = None
+    if rank == 0:
+        pk = peaks()
+        roofs = meson_rooflines(kstats, m, pk, args.steps)
+        tens = [r for r in roofs if r["bound"] == "tensor"]
+        dom = max(tens, key=lambda r: r["ms_per_step"]) if tens else None
+        issued = sum(8.0 * meson_split_products(k) * meson_cmacs(k, m)[0]
+                     for k in ("tc_gemm_meson_elem", "tc_gemm_meson_q", "tc_gemm_meson_x"))
+        tpeak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
+        cpu, parity = None, None
+        if not args.no_cpu_baseline:
+            cpu, C_ref = meson_cpu_baseline(m, v_h, U_h, tau_h, 1)
+            if not args.no_parity:
+                import importlib
+                sys.path.insert(0, os.path.join(ROOT, "tests"))
+                par = importlib.import_module("parity")
+                got = C[..., 1:2].cpu().numpy()
+                parity = {"reference": "FP64 oracle, sink timeslice t = 1 (the cpu_baseline sample)",
+                          "max_rel_err": par.max_c_error(got, C_ref[..., None])}
+        out = {
+            "metric": MESON_METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp16x6(f32 accumulate)",
+            "data": "synthetic (seeded orthonormal eigenvectors, Haar SU(3) links, Gaussian perambulators)",
+            "config": {"workload": m.name, "L": m.L, "nt": m.nt, "nv": m.nv, "np": m.np_, "nb": m.nb,
+                       "operators": nops, "nkeep": m.nkeep, "t_prune": m.t_prune, "t0_gevp": t0_gevp,
+                       "step": "one configuration: elementals (7 displacements, all t), C_ab(t) for all t, "
+                               "SVD pruning, GEVP of the pruned matrix",
+                       "parallelism": f"weak x{world} (configuration r on rank r)",
+                       "l2": "inputs larger than L2 (v is %.2f GB)" % (v.numel() * 8 / 1e9)},
+            "e2e": {"value": e2e_value, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(sum(l for l, _ in kstats.values())),
+            "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in sorted(kstats.items(),
+                                                                                  key=lambda kv: -kv[1][1])},
+            "roofline": None if dom is None else {**dom, "traffic": None},
+            "kernel_rooflines": roofs,
+            "whole_step": {"issued_tflops": issued / (ms_step / 1e3) / 1e12,
+                           "frac": issued / (ms_step / 1e3) / 1e12 / tpeak, "peak": tpeak,
+                           "note": "split products the three contraction families issue per configuration "
+                                   "over the whole step time"},
+            "clocks": clk,
+            "parity": parity,
+            "cpu_baseline": cpu,
+            "singular_values": res["sv"][0].cpu().numpy().tolist()[:12],
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
 def spawn_ranks(n: int) -> int:
     """bench.py --gpus N run without a launcher: start N ranks of this script
     under torch.distributed.run on this node (127.0.0.1) and return its exit
@@ -1137,14 +1398,18 @@ def main():
                     help="kernel variants of the three contraction sites, e.g. 0,0,0 (default: the library's)")
     ap.add_argument("--nt", type=int, default=0,
                     help="keep only the first NT timeslices (profiling a smaller case; not a bench number)")
+    ap.add_argument("--meson", default=None, choices=["charm", "small"],
+                    help="time the one-meson path on this workload instead (charm: L=24, N_t=48, N_v=200)")
     ap.add_argument("--np", type=int, default=0,
                     help="workloads 1-3: keep only the first NP momenta (profiling a smaller case; not a bench number)")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(spawn_ranks(args.gpus))
-    if args.warmup < 3 and args.impl == "ours" and args.workload == 5:
+    if args.warmup < 3 and args.impl == "ours" and (args.workload == 5 or args.meson):
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.meson and args.impl == "ours":
+        out = run_meson(args)
+    elif args.impl == "reference":
         out = run_reference(args)
     elif args.workload == 4:
         out = run_ensemble(args)

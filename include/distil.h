@@ -396,6 +396,74 @@ int distil_profile_enable(distil_ctx* ctx, int timing);
  * families seen into *count.  Waits for the recorded events to complete. */
 int distil_profile_read(distil_ctx* ctx, distil_kernel_stat* out, int max, int* count);
 
+/* ------------------------------------------------------------------ */
+/* One-meson operators with distillation profiles                      */
+/* ------------------------------------------------------------------ */
+/* Paper Sec. 4 ("Improved charmonium operators"): operators qbar Gamma q
+ * with Gamma in {gamma_0 gamma_5, gamma_0 gamma_5 gamma_i nabla_i,
+ * gamma_i BB_i}, N_B Gaussian distillation profiles for each, the
+ * 3 N_B x 3 N_B correlation matrix pruned by the singular vectors of its
+ * largest singular values at one time separation, then the GEVP
+ * (distil_gevp on the pruned matrix).  Only DISTIL_MIXED_FP16X6 is built
+ * (other modes: DISTIL_ENOTSUP).  gamma_0 is the Euclidean gamma_4 of the
+ * Dirac-Pauli basis above, gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4. */
+
+int distil_meson_elementals_workspace(int L, int nt, int nv, int np, int mode, size_t* bytes);
+
+/* phi[t][q][d][i][j] = sum_x exp(-i p_q.x) v_i(x)^dagger (D_d v_j)(x), the
+ * colour inner product of v_i with the displaced D_d v_j, d = 0..6 for
+ * 1, nabla_x, nabla_y, nabla_z, BB_x, BB_y, BB_z:
+ *   (nabla_k f)(x) = 1/2 [U_k(x) f(x+k) - U_k(x-k)^dagger f(x-k)]
+ *   (the symmetric gauge-covariant difference, periodic in space) and
+ *   BB_i = eps_ijk nabla_j nabla_k = nabla_j nabla_k - nabla_k nabla_j for
+ *   (i, j, k) cyclic, the right derivative acting first.
+ *   v    [nt][nv][L^3][3]        c64 device (distillation vectors)
+ *   U    [nt][3][L^3][3][3]      c64 device: U[t][k][s][a][b] = row a,
+ *                                column b of the link from s in direction k
+ *   mom  [np][3] int32           HOST, read during the call
+ *   phi  [nt][np][7][nv][nv]     c128 device, fully overwritten
+ * The products are formed exactly in double-float and contracted on the
+ * tensor cores in 4032-long K chunks (the elementals scheme of FP16X6).
+ * Sizes: 1 <= L <= 128, nt >= 1, 1 <= nv <= 1024, 1 <= np <= 16. */
+int distil_meson_elementals(distil_ctx* ctx, const void* v, const void* U, int L, int nt, int nv,
+                            const int32_t* mom, int np, int mode, void* phi, void* workspace,
+                            size_t ws_bytes, distil_stream stream);
+
+int distil_meson_correlate_workspace(int nv, int np, int nb, int mode, size_t* bytes);
+
+/* C[q][a][b][t] = -Tr[Phi_a(q, t) tau(t) Phibar_b(q, 0) gamma_5 tau(t)^dagger gamma_5]
+ * (the isovector connected correlator, source at t0 = 0, backward
+ * propagator from gamma_5-hermiticity) for operators a = 7 type + sigma
+ * (nb profiles sigma per type; 3 nb operators):
+ *   Phi_a    = sum_c Gamma_c (x) g Phi^(d_c) g      spin-major [4nv][4nv]
+ *   Phibar_b = sum_c gamma_4 Gamma_c^dagger gamma_4 (x) (g Phi^(d_c)(0) g)^dagger
+ *   type 0: Gamma = gamma_4 gamma_5, d = 0;  type 1: gamma_4 gamma_5 gamma_k,
+ *   d = 1 + k;  type 2: gamma_k, d = 4 + k  (k = x, y, z summed);
+ *   g = diag(prof[sigma]) multiplies both quark indices.
+ *   phi_snk [nt][np][7][nv][nv]  c128 device: sink elementals at t
+ *   phi_src [np][7][nv][nv]      c128 device: source elementals at t0 = 0
+ *   tau     [nt][4nv][4nv]       c64 device: tau(t, 0), spin-major
+ *   prof    [nb][nv]             f64 device
+ *   C       [np][3nb][3nb][nt]   c128 device, fully overwritten
+ * Two tensor-core GEMMs per (t, q) with K = 4 nv (Q_b = Phibar_b g5 tau^dagger
+ * g5, then X_b = tau Q_b) and a double-float reduction with the profiles.
+ * Sizes: nt >= 1, 1 <= nv <= 1024, 1 <= np <= 16, 1 <= nb <= 10. */
+int distil_meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, const void* tau,
+                           int nt, int nv, int np, const double* prof, int nb, int mode, void* C,
+                           void* workspace, size_t ws_bytes, distil_stream stream);
+
+/* Pruning (Sec. 4: the singular vectors of the n largest singular values
+ * of C at one time separation):  C(t_prune) = U S V^dagger,
+ *   Un[q][a][m]   = column m of U (m < nkeep), scaled so that its
+ *                   largest-modulus component (the first of equal ones) is
+ *                   real and positive                     c128 device
+ *   Ct[q][m][n][t] = (Un^dagger C(t) Un)[m][n]           c128 device
+ *   sv[q][a]       = the singular values, descending     f64 device or NULL
+ *   C [np][nops][nops][nt] c128 device.  One-sided Jacobi SVD in FP64.
+ * Sizes: 1 <= nops <= 32, 1 <= nkeep <= min(nops, 16), 0 <= t_prune < nt. */
+int distil_meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt, int t_prune, int nkeep,
+                       void* Ct, void* Un, double* sv, distil_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,15 @@ int optimal_launch(distil_ctx* ctx, const void* C, int np, int nb, int nt, const
 int eigen_profiles_launch(distil_ctx* ctx, const double* lam, int nt, int nv, const double* sigma, int nb,
                           double* prof, cudaStream_t s);
 
+size_t meson_elementals_workspace(int L, int nt, int nv, int np);
+int meson_elementals(distil_ctx* ctx, const void* v, const void* U, int L, int nt, int nv, const int32_t* mom,
+                     int np, void* phi, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t meson_correlate_workspace(int nv, int np, int nb);
+int meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, const void* tau, int nt, int nv,
+                    int np, const double* prof, int nb, void* C, void* ws, size_t ws_bytes, cudaStream_t s);
+int meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt, int tp, int nkeep, void* Ct, void* Un,
+                double* sv, cudaStream_t s);
+
 Profiler& profiler(distil_ctx* ctx) { return *ctx->prof; }
 
 // Lowest index of a NaN or Inf among x[0, count) into the 64-bit word *slot
@@ -290,6 +299,101 @@ int distil_cgemm(distil_ctx* ctx, const void* A, const void* B, void* C, int M, 
     return DISTIL_ENOMEM;
   }
   return cgemm_mixed(ctx, mode, A, B, C, M, N, K, batch, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------ meson path
+
+static constexpr int MS_LIMIT_MOM = 16, MS_LIMIT_NB = 10, MS_LIMIT_NV = 1024, MS_LIMIT_L = 128;
+
+int distil_meson_elementals_workspace(int L, int nt, int nv, int np, int mode, size_t* bytes) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
+  if (mode != DISTIL_MIXED_FP16X6) {
+    set_error("distil_meson_elementals_workspace: mode %d not supported (FP16X6 only)", mode);
+    return DISTIL_ENOTSUP;
+  }
+  DISTIL_CHECK_ARG(L >= 1 && L <= MS_LIMIT_L && nt >= 1 && nv >= 1 && nv <= MS_LIMIT_NV && np >= 1 &&
+                       np <= MS_LIMIT_MOM,
+                   "distil_meson_elementals_workspace: bad sizes");
+  *bytes = meson_elementals_workspace(L, nt, nv, np);
+  return DISTIL_OK;
+}
+
+int distil_meson_elementals(distil_ctx* ctx, const void* v, const void* U, int L, int nt, int nv,
+                            const int32_t* mom, int np, int mode, void* phi, void* workspace, size_t ws_bytes,
+                            distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  if (mode != DISTIL_MIXED_FP16X6) {
+    set_error("distil_meson_elementals: mode %d not supported (FP16X6 only)", mode);
+    return DISTIL_ENOTSUP;
+  }
+  DISTIL_CHECK_ARG(L >= 1 && L <= MS_LIMIT_L, "distil_meson_elementals: L=%d outside [1,%d]", L, MS_LIMIT_L);
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && nv <= MS_LIMIT_NV, "distil_meson_elementals: nt >= 1, 1 <= nv <= %d",
+                   MS_LIMIT_NV);
+  DISTIL_CHECK_ARG(np >= 1 && np <= MS_LIMIT_MOM, "distil_meson_elementals: 1 <= np <= %d", MS_LIMIT_MOM);
+  DISTIL_CHECK_ARG(v && U && mom && phi && workspace, "distil_meson_elementals: null pointer");
+  DISTIL_CHECK_ARG(aligned(v, 8) && aligned(U, 8) && aligned(phi, 16) && aligned(workspace, 256),
+                   "distil_meson_elementals: misaligned pointer (arrays to their element, workspace to 256 bytes)");
+  const size_t need = meson_elementals_workspace(L, nt, nv, np);
+  if (ws_bytes < need) {
+    set_error("distil_meson_elementals: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  return meson_elementals(ctx, v, U, L, nt, nv, mom, np, phi, workspace, ws_bytes,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_meson_correlate_workspace(int nv, int np, int nb, int mode, size_t* bytes) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
+  if (mode != DISTIL_MIXED_FP16X6) {
+    set_error("distil_meson_correlate_workspace: mode %d not supported (FP16X6 only)", mode);
+    return DISTIL_ENOTSUP;
+  }
+  DISTIL_CHECK_ARG(nv >= 1 && nv <= MS_LIMIT_NV && np >= 1 && np <= MS_LIMIT_MOM && nb >= 1 && nb <= MS_LIMIT_NB,
+                   "distil_meson_correlate_workspace: bad sizes");
+  *bytes = meson_correlate_workspace(nv, np, nb);
+  return DISTIL_OK;
+}
+
+int distil_meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, const void* tau, int nt,
+                           int nv, int np, const double* prof, int nb, int mode, void* C, void* workspace,
+                           size_t ws_bytes, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  if (mode != DISTIL_MIXED_FP16X6) {
+    set_error("distil_meson_correlate: mode %d not supported (FP16X6 only)", mode);
+    return DISTIL_ENOTSUP;
+  }
+  DISTIL_CHECK_ARG(nt >= 1 && nv >= 1 && nv <= MS_LIMIT_NV, "distil_meson_correlate: nt >= 1, 1 <= nv <= %d",
+                   MS_LIMIT_NV);
+  DISTIL_CHECK_ARG(np >= 1 && np <= MS_LIMIT_MOM, "distil_meson_correlate: 1 <= np <= %d", MS_LIMIT_MOM);
+  DISTIL_CHECK_ARG(nb >= 1 && nb <= MS_LIMIT_NB, "distil_meson_correlate: nb=%d outside [1,%d]", nb, MS_LIMIT_NB);
+  DISTIL_CHECK_ARG(phi_snk && phi_src && tau && prof && C && workspace, "distil_meson_correlate: null pointer");
+  DISTIL_CHECK_ARG(aligned(phi_snk, 16) && aligned(phi_src, 16) && aligned(tau, 8) && aligned(prof, 8) &&
+                       aligned(C, 16) && aligned(workspace, 256),
+                   "distil_meson_correlate: misaligned pointer (arrays to their element, workspace to 256 bytes)");
+  const size_t need = meson_correlate_workspace(nv, np, nb);
+  if (ws_bytes < need) {
+    set_error("distil_meson_correlate: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  return meson_correlate(ctx, phi_snk, phi_src, tau, nt, nv, np, prof, nb, C, workspace, ws_bytes,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+int distil_meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt, int t_prune, int nkeep, void* Ct,
+                       void* Un, double* sv, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(C && Ct && Un, "distil_meson_prune: null pointer");
+  DISTIL_CHECK_ARG(np >= 1 && nt >= 1 && nops >= 1 && nops <= 32, "distil_meson_prune: np, nt >= 1, 1 <= nops <= 32");
+  DISTIL_CHECK_ARG(nkeep >= 1 && nkeep <= nops && nkeep <= 16, "distil_meson_prune: 1 <= nkeep <= min(nops, 16)");
+  DISTIL_CHECK_ARG(t_prune >= 0 && t_prune < nt, "distil_meson_prune: t_prune=%d outside [0,%d)", t_prune, nt);
+  DISTIL_CHECK_ARG(aligned(C, 16) && aligned(Ct, 16) && aligned(Un, 16) && aligned(sv, 8),
+                   "distil_meson_prune: misaligned pointer");
+  return meson_prune(ctx, C, np, nops, nt, t_prune, nkeep, Ct, Un, sv, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int distil_mode_supported(int mode) {

@@ -39,7 +39,8 @@ EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_device_status", "distil_set_tuning", "distil_get_tuning",
            "distil_plan_workspace", "distil_plan_create", "distil_plan_run", "distil_plan_info",
            "distil_plan_destroy", "distil_set_wait_limit", "distil_scan_finite",
-           "distil_profiles_eigen"]
+           "distil_profiles_eigen", "distil_meson_elementals_workspace", "distil_meson_elementals",
+           "distil_meson_correlate_workspace", "distil_meson_correlate", "distil_meson_prune"]
 
 _lib = None
 _ctx = {}
@@ -133,6 +134,19 @@ def _declare(L):
     L.distil_mode_supported.restype = c_int
     L.distil_profile_enable.argtypes = [c_void_p, c_int]
     L.distil_profile_enable.restype = c_int
+    L.distil_meson_elementals_workspace.argtypes = [c_int, c_int, c_int, c_int, c_int, P(c_size_t)]
+    L.distil_meson_elementals_workspace.restype = c_int
+    L.distil_meson_elementals.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, P(ctypes.c_int32),
+                                          c_int, c_int, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.distil_meson_elementals.restype = c_int
+    L.distil_meson_correlate_workspace.argtypes = [c_int, c_int, c_int, c_int, P(c_size_t)]
+    L.distil_meson_correlate_workspace.restype = c_int
+    L.distil_meson_correlate.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                         c_int, c_int, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.distil_meson_correlate.restype = c_int
+    L.distil_meson_prune.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                                     c_void_p, c_void_p]
+    L.distil_meson_prune.restype = c_int
     L.distil_profile_read.argtypes = [c_void_p, P(KernelStat), c_int, P(c_int)]
     L.distil_profile_read.restype = c_int
 
@@ -524,3 +538,73 @@ class Plan:
             _lib.distil_plan_destroy(h)
             self.handle = None
 
+
+# ------------------------------------------------------------------ mesons
+
+
+def meson_elementals_workspace(L: int, nt: int, nv: int, np_: int, mode="fp16x6") -> int:
+    b = ctypes.c_size_t()
+    _check(lib().distil_meson_elementals_workspace(L, nt, nv, np_, _mode(mode), ctypes.byref(b)))
+    return b.value
+
+
+def meson_elementals(v, U, L: int, mom, mode="fp16x6", out=None, workspace=None, stream=None):
+    """v [nt][nv][L^3][3] c64, U [nt][3][L^3][3][3] c64 (GPU); mom [np][3]
+    ints (host) -> phi [nt][np][7][nv][nv] c128."""
+    import torch
+    mode = _mode(mode)
+    nt, nv = int(v.shape[0]), int(v.shape[1])
+    V3 = L ** 3
+    assert v.is_cuda and v.is_contiguous() and v.dtype == torch.complex64 and tuple(v.shape[2:]) == (V3, 3)
+    assert U.is_cuda and U.is_contiguous() and U.dtype == torch.complex64 and tuple(U.shape) == (nt, 3, V3, 3, 3)
+    mom_np = np.ascontiguousarray(np.asarray(mom, dtype=np.int32).reshape(-1, 3))
+    np_ = mom_np.shape[0]
+    if out is None:
+        out = torch.empty((nt, np_, 7, nv, nv), dtype=torch.complex128, device=v.device)
+    if workspace is None:
+        workspace = _workspace(meson_elementals_workspace(L, nt, nv, np_, mode), v.device)
+    _check(lib().distil_meson_elementals(context(v.device.index or 0), _ptr(v), _ptr(U), L, nt, nv,
+                                         mom_np.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), np_, mode,
+                                         _ptr(out), _ptr(workspace), _nbytes(workspace), _stream(stream)))
+    return out
+
+
+def meson_correlate_workspace(nv: int, np_: int, nb: int, mode="fp16x6") -> int:
+    b = ctypes.c_size_t()
+    _check(lib().distil_meson_correlate_workspace(nv, np_, nb, _mode(mode), ctypes.byref(b)))
+    return b.value
+
+
+def meson_correlate(phi_snk, phi_src, tau, prof, mode="fp16x6", out=None, workspace=None, stream=None):
+    """phi_snk [nt][np][7][nv][nv], phi_src [np][7][nv][nv] (c128), tau
+    [nt][4nv][4nv] (c64), prof [nb][nv] (f64) -> C [np][3nb][3nb][nt] c128."""
+    import torch
+    mode = _mode(mode)
+    nt, np_, _, nv, _ = (int(x) for x in phi_snk.shape)
+    nb = int(prof.shape[0])
+    for x in (phi_snk, phi_src, tau, prof):
+        assert x.is_cuda and x.is_contiguous()
+    assert phi_snk.dtype == torch.complex128 and phi_src.dtype == torch.complex128
+    assert tau.dtype == torch.complex64 and prof.dtype == torch.float64
+    if out is None:
+        out = torch.empty((np_, 3 * nb, 3 * nb, nt), dtype=torch.complex128, device=tau.device)
+    if workspace is None:
+        workspace = _workspace(meson_correlate_workspace(nv, np_, nb, mode), tau.device)
+    _check(lib().distil_meson_correlate(context(tau.device.index or 0), _ptr(phi_snk), _ptr(phi_src), _ptr(tau),
+                                        nt, nv, np_, _ptr(prof), nb, mode, _ptr(out), _ptr(workspace),
+                                        _nbytes(workspace), _stream(stream)))
+    return out
+
+
+def meson_prune(C, t_prune: int, nkeep: int, stream=None):
+    """C [np][nops][nops][nt] c128 -> (Ct [np][nkeep][nkeep][nt], Un
+    [np][nops][nkeep], singular values [np][nops])."""
+    import torch
+    np_, nops, _, nt = (int(x) for x in C.shape)
+    assert C.is_cuda and C.is_contiguous() and C.dtype == torch.complex128
+    Ct = torch.empty((np_, nkeep, nkeep, nt), dtype=torch.complex128, device=C.device)
+    Un = torch.empty((np_, nops, nkeep), dtype=torch.complex128, device=C.device)
+    sv = torch.empty((np_, nops), dtype=torch.float64, device=C.device)
+    _check(lib().distil_meson_prune(context(C.device.index or 0), _ptr(C), np_, nops, nt, int(t_prune), int(nkeep),
+                                    _ptr(Ct), _ptr(Un), _ptr(sv), _stream(stream)))
+    return Ct, Un, sv
