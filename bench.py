@@ -1332,7 +1332,11 @@ def run_meson(args):
                 par = importlib.import_module("parity")
                 got = C[..., 1:2].cpu().numpy()
                 parity = {"reference": "FP64 oracle, sink timeslice t = 1 (the cpu_baseline sample)",
-                          "max_rel_err": par.max_c_error(got, C_ref[..., None])}
+                          "max_operator_scaled_err": par.max_c_operator_scaled_error(got, C_ref[..., None]),
+                          "max_matrix_scaled_err": par.max_c_scaled_error(got, C_ref[..., None]),
+                          "max_rel_err": par.max_c_error(got, C_ref[..., None]),
+                          "gate": "operator-scaled error (|dC_ab| / sqrt(R_a R_b), R = largest |C| of an "
+                                  "operator's row or column) < 1e-6"}
         out = {
             "metric": MESON_METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

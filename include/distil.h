@@ -399,7 +399,7 @@ int distil_profile_read(distil_ctx* ctx, distil_kernel_stat* out, int max, int* 
 /* ------------------------------------------------------------------ */
 /* One-meson operators with distillation profiles                      */
 /* ------------------------------------------------------------------ */
-/* Paper Sec. 4 ("Improved charmonium operators"): operators qbar Gamma q
+/* Paper Sec. 2.3 ("Improved charmonium operators"): operators qbar Gamma q
  * with Gamma in {gamma_0 gamma_5, gamma_0 gamma_5 gamma_i nabla_i,
  * gamma_i BB_i}, N_B Gaussian distillation profiles for each, the
  * 3 N_B x 3 N_B correlation matrix pruned by the singular vectors of its
@@ -452,7 +452,7 @@ int distil_meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi
                            int nt, int nv, int np, const double* prof, int nb, int mode, void* C,
                            void* workspace, size_t ws_bytes, distil_stream stream);
 
-/* Pruning (Sec. 4: the singular vectors of the n largest singular values
+/* Pruning (Sec. 2.3: the singular vectors of the n largest singular values
  * of C at one time separation):  C(t_prune) = U S V^dagger,
  *   Un[q][a][m]   = column m of U (m < nkeep), scaled so that its
  *                   largest-modulus component (the first of equal ones) is

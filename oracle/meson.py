@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py`` may import or run this module.  It shares no
 code, table or layout helper with the CUDA library: it is a plain, slow,
 obviously correct restatement of the definitions, in complex128 throughout.
 
-What it computes (paper Sec. 4, "Improved charmonium operators": one-meson
+What it computes (paper Sec. 2.3, "Improved charmonium operators": one-meson
 operators qbar Gamma q with Gamma in {gamma_0 gamma_5, gamma_0 gamma_5
 gamma_i nabla_i, gamma_i BB_i}, each with N_B = 7 Gaussian distillation
 profiles, the 21 x 21 correlation matrix pruned to 8 x 8 by the singular

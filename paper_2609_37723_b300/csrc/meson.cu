@@ -1,4 +1,4 @@
-// One-meson operators with distillation profiles (paper Sec. 4, "Improved
+// One-meson operators with distillation profiles (paper Sec. 2.3, "Improved
 // charmonium operators") on tcgen05 tensor cores:
 //
 //  elementals  Phi^d[p]_ij = sum_x exp(-i p.x) v_i(x)^dagger (D_d v_j)(x),
@@ -48,6 +48,16 @@ static_assert(MS_KC % 3 == 0 && MS_KC % 16 == 0, "chunks of whole sites and K bl
 constexpr int MS_MAX_MOM = 16;
 constexpr int MS_MAX_NB = 10;  // 3 N_B <= 30 operators: one warp lane per row in the SVD
 constexpr int MS_RED_CHUNKS = 8;  // i chunks of the correlator reduction
+// Norm caps (split writers: the scaled slices of a capped row have 2-norm
+// <= 2^bits) on the operand rows that can sum coherently against rows of
+// the other operand, whose leading-slice sums must stay below 2^24 to add
+// exactly: in the elementals v_j (d = 0) against exp(-i p.x) conj(v_i) at
+// p = 0 (sum_x |v_i|^2 = 1 on the diagonal); in GEMM 2 the type-0 source
+// rows of Q (Phibar ~ identity in mode space, so Q ~ g5 tau^dagger g5)
+// against the tau rows.  2^11 x 2^12 keeps those sums below 2^23.  Rows that
+// sum with random signs keep their max-based exponents (and their bits):
+// capping every row cost up to five bits of GEMM 2.
+constexpr int MS_CAP_A = 11, MS_CAP_B = 12;
 
 // ------------------------------------------------------------ spin tables
 // Gamma[alpha][perm[alpha]] = phase[alpha] (a signed permutation, phases in
@@ -318,6 +328,9 @@ struct DispSrc {  // rows u (7 nv) + d nv + j
   }
   __device__ __forceinline__ CDF operator()(long long r, int kk) const { return row(r)(kk); }
   __device__ __forceinline__ float2 approx(long long r, int kk) const { return row(r).approx(kk); }
+  __device__ __forceinline__ int norm_bits(long long r) const {
+    return (int)((r % ((long long)MS_NDISP * nv)) / nv) == 0 ? MS_CAP_A : 0;  // d = 0: v_j itself
+  }
 };
 
 // B operand of the elementals: exp(-i p_q.x) conj(v_i^a(x)) at K = 3 x + a
@@ -355,6 +368,10 @@ struct PhConjSrc {  // rows u R + q nv + i
   }
   __device__ __forceinline__ CDF operator()(long long r, int kk) const { return row(r)(kk); }
   __device__ __forceinline__ float2 approx(long long r, int kk) const { return row(r).approx(kk); }
+  __device__ __forceinline__ int norm_bits(long long r) const {
+    const int q = (int)((r % ((long long)m.np * nv)) / nv);
+    return (m.mom[q][0] | m.mom[q][1] | m.mom[q][2]) == 0 ? MS_CAP_B : 0;  // p = 0
+  }
 };
 
 // phi[u][q][d][i][j] = Phi_acc[u][(d, j)][(q, i)] as complex128, through
@@ -683,7 +700,8 @@ struct C64Rows {
 // A operand of GEMM 2: row (b, L) = Q_b[.][L] = C1[L][b 4nv + K]
 struct QRows {
   const CDF* c1;
-  int n4, nops;
+  int n4, nops, nb;
+  __device__ __forceinline__ int norm_bits(long long r) const { return r / n4 < nb ? MS_CAP_A : 0; }  // type 0
   __device__ __forceinline__ CDF operator()(long long r, int k) const {
     const long long b = r / n4, L = r - b * n4;
     return ld_cdf(c1 + L * ((long long)nops * n4) + b * n4 + k);
@@ -875,7 +893,8 @@ int meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, c
     const float2* tau_t = reinterpret_cast<const float2*>(tau) + (long long)t * n4 * n4;
     tts.tau = tau_t;
     DISTIL_TRY((split_rows<false, true, NB>(ctx, "split_meson_tautilde", tts, n4, B1, H, w.eB1, s)));
-    DISTIL_TRY((split_rows<false, true, NB>(ctx, "split_meson_tau", C64Rows{tau_t, n4}, n4, B2, H, w.eB2, s)));
+    DISTIL_TRY((split_rows<false, true, NB>(ctx, "split_meson_tau", C64Rows{tau_t, n4}, n4, B2, H, w.eB2, s,
+                                            nullptr, MS_CAP_B)));
     {
       Launch Lc(ctx, "meson_corr_setup", s);
       meson_to_cdf_kernel<<<tgrid, dim3(32, 8), 0, s>>>(
@@ -894,7 +913,7 @@ int meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, c
                            : mcorr_gemm<32>(ctx, "tc_gemm_meson_q", A1, B1, cfg, epi, s));
       }
       // GEMM 2: D[(b, L)][I] = (tau Q_b)[I][L] = X_b[I][L], stored XT[(b, L)][I]
-      DISTIL_TRY((split_rows<false, true, NA>(ctx, "split_meson_q", QRows{w.C1, n4, nops}, M, A2, H, w.eA2, s)));
+      DISTIL_TRY((split_rows<false, true, NA>(ctx, "split_meson_q", QRows{w.C1, n4, nops, nb}, M, A2, H, w.eA2, s)));
       cfg.a = tc::OpMap{1, 1, 1, 0, 0, (int)M, w.eA2};
       cfg.b = tc::OpMap{1, 1, 1, 0, 0, n4, w.eB2};
       {

@@ -225,6 +225,37 @@ __device__ __forceinline__ auto bind_row(const Src& src, long long r) {
     return RowOf<Src>{&src, r};
 }
 
+// Optional cap on a row's scaled 2-norm: with norm_bits > 0 the exponent is
+// raised until 2^(H - e) ||x|| <= 2^norm_bits (ss = ||x||^2, padded for its
+// FP32 rounding).  Two rows capped at 2^11 keep every leading-slice sum
+// |sum_k hi_a hi_b| <= ||hi_a|| ||hi_b|| below 2^24 whatever the K and
+// however aligned the rows (a coherent sum such as sum_x |v(x)|^2 reaches
+// that bound long before a random-sign one), so the class-0 accumulation
+// stays exact.  Off (0) for operands whose rows are known to sum with random
+// signs.
+__device__ __forceinline__ int norm_capped_exponent(int e, float ss, int H, int norm_bits) {
+  if (norm_bits <= 0 || !(ss > 0.f)) return e;
+  int en;
+  frexpf(sqrtf(ss) * (1.f + 1.f / 4096.f), &en);  // ||x|| < 2^en
+  const int ec = H - norm_bits + en;
+  return ec > e ? ec : e;
+}
+
+// A source may give each row its own norm cap (Src::norm_bits(r), 0 = none)
+// in place of the split's one value: only rows that can sum coherently
+// against the other operand need one.
+template <class S, class = void>
+struct has_norm_bits : std::false_type {};
+template <class S>
+struct has_norm_bits<S, std::void_t<decltype(std::declval<const S&>().norm_bits(0LL))>> : std::true_type {};
+template <class Src>
+__device__ __forceinline__ int row_norm_bits(const Src& src, long long r, int dflt) {
+  if constexpr (has_norm_bits<Src>::value)
+    return src.norm_bits(r);
+  else
+    return dflt;
+}
+
 // Split rows of a complex operand into 2*NPC planes with a per-row exponent.
 // Global row r = coord * img.rows + rr goes to plane image img (tc_gemm.cuh:
 // PlaneImg; plane 2 i + re/im holds piece i) at coordinate coord, row rr,
@@ -235,7 +266,8 @@ __device__ __forceinline__ auto bind_row(const Src& src, long long r) {
 // as a complex double-float, Src::approx(r, k) an FP32 estimate of it.
 template <bool BF16, bool FIXED, int NPC, class Src, int ROT = 0>
 __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrows, tc::PlaneImg img, int H,
-                                                         int* __restrict__ exps, float* __restrict__ norms) {
+                                                         int* __restrict__ exps, float* __restrict__ norms,
+                                                         int norm_bits) {
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= nrows) return;
@@ -252,7 +284,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
     ss += __shfl_xor_sync(0xffffffffu, ss, o);
   }
   // the FP32 estimate may sit slightly below the true magnitude: pad by 2^-16
-  const int e = row_exponent(m * (1.f + 1.f / 65536.f));
+  const int e =
+      norm_capped_exponent(row_exponent(m * (1.f + 1.f / 65536.f)), ss, H, row_norm_bits(src, r, norm_bits));
   if (lane == 0) {
     exps[r] = e;
     if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
@@ -273,7 +306,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(Src src, long long nrow
 // the exponent comes from the exact maximum.
 template <bool BF16, bool FIXED, int NPC, int PER, class Src, int ROT = 0>
 __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::PlaneImg img, int H,
-                                                                int* __restrict__ exps, float* __restrict__ norms) {
+                                                                int* __restrict__ exps, float* __restrict__ norms,
+                                                                int norm_bits) {
   __shared__ float red_m[16], red_s[16];
   __shared__ int sh_e;
   const long long r = blockIdx.x;
@@ -297,7 +331,8 @@ __global__ void __launch_bounds__(512) split_rows_cached_kernel(Src src, tc::Pla
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < 16; ++w) { m = fmaxf(m, red_m[w]); ss += red_s[w]; }
-    sh_e = row_exponent(m * (1.f + 1.f / 65536.f));
+    sh_e =
+        norm_capped_exponent(row_exponent(m * (1.f + 1.f / 65536.f)), ss, H, row_norm_bits(src, r, norm_bits));
     exps[r] = sh_e;
     if (norms) norms[r] = sqrtf(ss) * (1.f + 1e-5f);
   }
@@ -333,7 +368,7 @@ static __global__ void img_zero_kpad_kernel(tc::PlaneImg img) {
 
 template <bool BF16, bool FIXED, int NPC, class Src, int ROT = 0>
 inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long long nrows, const tc::PlaneImg& img,
-                      int H, int* exps, cudaStream_t s, float* norms = nullptr) {
+                      int H, int* exps, cudaStream_t s, float* norms = nullptr, int norm_bits = 0) {
   if (nrows <= 0) return DISTIL_OK;
   if (img.planes != 2 * NPC || img.ptot != img.planes || img.p0 != 0 || nrows > (long long)img.coords * img.rows ||
       img.kblocks * 16 < img.K) {
@@ -344,12 +379,15 @@ inline int split_rows(distil_ctx* ctx, const char* name, const Src& src, long lo
   const long long threads = nrows * 32;
   Launch L(ctx, name, s);
   if (K > 2048 && K <= 4096)
-    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src, ROT><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
+    split_rows_cached_kernel<BF16, FIXED, NPC, 8, Src, ROT><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms,
+                                                                                          norm_bits);
   else if (K > 1024 && K <= 2048)
-    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src, ROT><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms);
+    split_rows_cached_kernel<BF16, FIXED, NPC, 4, Src, ROT><<<(unsigned)nrows, 512, 0, s>>>(src, img, H, exps, norms,
+                                                                                          norm_bits);
   else
     split_rows_kernel<BF16, FIXED, NPC, Src, ROT><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, nrows, img,
-                                                                                                     H, exps, norms);
+                                                                                                     H, exps, norms,
+                                                                                                     norm_bits);
   DISTIL_LAUNCH_CHECK();
   return DISTIL_OK;
 }

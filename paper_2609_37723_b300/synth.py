@@ -24,7 +24,7 @@ Random streams: numpy PCG64 seeded by SeedSequence(2609, spawn_key=(config,
 cfg, t, field)) with field 0 = eigenvectors, 1 = perambulator, 2 = N_v draw,
 3 = Laplacian eigenvalues, 4 = gauge links.
 
-Meson workloads (Sec. 4 of the paper, "Improved charmonium operators") add
+Meson workloads (Sec. 2.3 of the paper, "Improved charmonium operators") add
 spatial gauge links U[t][k][s][a][b] (direction k = x, y, z; row a, column
 b), each an SU(3) matrix drawn from the Haar measure; the covariant
 derivatives of the meson operators read them.
@@ -224,7 +224,7 @@ class MesonProblem:
 
 
 def meson_config(which: str, cfg: int = 0) -> MesonProblem:
-    """Meson workloads shaped like the charmonium study (Sec. 4: N_f = 2,
+    """Meson workloads shaped like the charmonium study (Sec. 2.3: N_f = 2,
     24^3 x 48, N_v = 200, seven Gaussian profiles for each of three Gammas
     giving a 21 x 21 matrix pruned to 8 x 8):
       "charm"  L = 24, N_t = 48, N_v = 200, p = 0, perambulators complex64

@@ -49,3 +49,21 @@ def c_scaled_errors(got, ref) -> np.ndarray:
 
 def max_c_scaled_error(got, ref) -> float:
     return float(c_scaled_errors(got, ref).max())
+
+
+def c_operator_scaled_errors(got, ref) -> np.ndarray:
+    """Per-entry error relative to the magnitude of the two operators the
+    entry couples: |dC_ab(t)| / sqrt(R_a(t) R_b(t)), R_a = the largest
+    |C| in row a or column a at (p, t).  For matrices whose operators differ
+    in magnitude by orders (derivative and profile operators of very
+    different widths), where single entries can be 1e-5 of the largest one."""
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    A = np.abs(ref)
+    R = np.maximum(A.max(axis=2), A.max(axis=1))
+    scale = np.sqrt(R[:, :, None, :] * R[:, None, :, :])
+    return np.abs(got - ref) / np.maximum(scale, 1e-300)
+
+
+def max_c_operator_scaled_error(got, ref) -> float:
+    return float(c_operator_scaled_errors(got, ref).max())
