@@ -1126,10 +1126,13 @@ def _meson_eig_worker(args):
     return len(jobs)
 
 
-def meson_inputs(which: str, cfg: int, workers: int):
+def meson_inputs(which: str, cfg: int, workers: int, nt: int = 0):
     """Host inputs of one meson configuration: v, U, tau (numpy, the bytes the
-    tests draw); the eigenvectors in parallel spawned processes."""
+    tests draw); the eigenvectors in parallel spawned processes.  nt > 0
+    keeps the first nt timeslices (a smaller case for profilers)."""
     m = synth.meson_config(which, cfg)
+    if nt > 0:
+        m.base = dataclasses.replace(m.base, nt=min(nt, m.nt))
     shape = (m.nt, m.nv, m.V3, 3)
     dtype = np.dtype(m.dtype)
     if workers > 1 and m.nt > 1:
@@ -1231,7 +1234,7 @@ def run_meson(args):
     which = args.meson
     workers = min(32, os.cpu_count() or 1)
     log(f"generating meson workload {which}, configuration {rank}")
-    m, v_h, U_h, tau_h = meson_inputs(which, rank, workers)   # before any CUDA call
+    m, v_h, U_h, tau_h = meson_inputs(which, rank, workers, args.nt)   # before any CUDA call
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)

@@ -13,11 +13,11 @@
 //  prune       the left singular vectors U_n of C(t_p) for its n largest
 //              singular values and Ct(t) = U_n^dagger C(t) U_n.
 //
-// Elementals, per batch of timeslices: the three nabla_k v fields are formed
-// once in double-float (exact FP32 products summed by compensated dot
-// products); then K = (site, colour) runs in chunks of MS_KC values: the A
-// operand rows (d, j) are v, the stored nabla fields, or BB formed from them
-// on the fly in the split writer; the B operand rows (p, i) are
+// Elementals, per batch of timeslices: the three nabla_k v fields and then the
+// three BB_i v fields are formed once in double-float (exact FP32 products
+// summed by compensated dot products); then K = (site, colour) runs in chunks
+// of MS_KC values: the A operand rows (d, j) are v or the stored displaced
+// fields; the B operand rows (p, i) are
 // exp(-i p.x) conj(v_i); the tensor cores accumulate each chunk and the
 // epilogue adds it into a double-float Phi_acc[(d, j)][(p, i)].
 //
@@ -180,14 +180,12 @@ __device__ __forceinline__ CDF cdf_iph(CDF z, int ph) {
   }
 }
 
-__device__ __forceinline__ int site_step(int s, int L, int k, int step) {
-  int x = s % L;
-  const int yz = s / L;
-  int y = yz % L, z = yz / L;
-  if (k == 0) x = (x + step + L) % L;
-  else if (k == 1) y = (y + step + L) % L;
-  else z = (z + step + L) % L;
-  return x + L * (y + L * z);
+// Sites s + e_k and s - e_k on the periodic L^3 lattice, s = x + L (y + L z),
+// from the coordinates c[3] = (x, y, z) of s.
+__device__ __forceinline__ void neighbours(int s, const int (&c)[3], int L, int k, int& sp, int& sm) {
+  const int stride = k == 0 ? 1 : k == 1 ? L : L * L;
+  sp = c[k] == L - 1 ? s - (L - 1) * stride : s + stride;
+  sm = c[k] == 0 ? s + (L - 1) * stride : s - stride;
 }
 
 // (nabla_k f)(s)_a accumulated (times sg) into re, im:
@@ -234,7 +232,8 @@ __device__ __forceinline__ void nabla_acc_df(Dot2& re, Dot2& im, float sg, const
   }
 }
 
-// nabla fields N[u][k][j][s][a] = (nabla_k v_j)(s)_a for the timeslices of a
+// nabla fields N[u][k][j][s][a] = (nabla_k v_j)(s)_a (fields 0..2 of the
+// batch's displaced-field buffer, [u][6][nv][V3][3]) for the timeslices of a
 // batch: one thread per (u, k, j, s), three colours.
 __global__ void __launch_bounds__(256) meson_nabla_kernel(const float2* __restrict__ v, const float2* __restrict__ U,
                                                           int L, int nv, int tb, CDF* __restrict__ out) {
@@ -249,13 +248,57 @@ __global__ void __launch_bounds__(256) meson_nabla_kernel(const float2* __restri
   const long long u = r / (3LL * nv);
   const float2* f = v + (u * nv + j) * V3 * 3;
   const float2* Uk = U + (u * 3 + k) * V3 * 9;
-  const int sp = site_step(s, L, k, 1), sm = site_step(s, L, k, -1);
-  CDF* o = out + idx * 3;
+  const int c[3] = {s % L, (s / L) % L, s / (L * L)};
+  int sp, sm;
+  neighbours(s, c, L, k, sp, sm);
+  CDF* o = out + ((u * 6 + k) * nv + j) * V3 * 3 + (long long)s * 3;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     Dot2 re, im;
     nabla_acc_f(re, im, 1.f, Uk, f, sp, s, sm, a);
     o[a] = cdf_make(df_half(re.get()), df_half(im.get()));
+  }
+}
+
+// BB fields (fields 3..5 of the buffer): BB_i v_j = nabla_j'(N_k') -
+// nabla_k'(N_j') for (i, j', k') cyclic, from the nabla fields N_k = fields
+// 0..2.  One thread per (u, j, s), all three i and colours: the outer
+// derivative in direction m enters BB_(m+2) with N_(m+1) and BB_(m+1) with
+// -N_(m+2), so each link pair U_m(s), U_m(s - m) serves two fields and each
+// nabla field is read once (a thread per (u, i, j, s) ran no faster: it
+// halved the registers but doubled the field reads and hit the L2 tag rate).
+__global__ void __launch_bounds__(128) meson_bb_kernel(const float2* __restrict__ U, int L, int nv, int tb,
+                                                       CDF* __restrict__ N) {
+  const long long V3 = (long long)L * L * L;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)tb * nv * V3) return;
+  const int s = (int)(idx % V3);
+  const long long r = idx / V3;
+  const int j = (int)(r % nv);
+  const long long u = r / nv;
+  const int c[3] = {s % L, (s / L) % L, s / (L * L)};
+  const long long fs = (long long)nv * V3 * 3;  // stride of one field
+  CDF* Nu = N + u * 6 * fs + (long long)j * V3 * 3;
+  Dot2 re[3][3], im[3][3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    int sp, sm;
+    neighbours(s, c, L, m, sp, sm);
+    const float2* Um = U + (u * 3 + m) * V3 * 9;
+    const int i_plus = (m + 2) % 3, i_minus = (m + 1) % 3;
+    const CDF* f_plus = Nu + ((m + 1) % 3) * fs;
+    const CDF* f_minus = Nu + ((m + 2) % 3) * fs;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      nabla_acc_df(re[i_plus][a], im[i_plus][a], 1.f, Um, f_plus, sp, s, sm, a);
+      nabla_acc_df(re[i_minus][a], im[i_minus][a], -1.f, Um, f_minus, sp, s, sm, a);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    CDF* o = Nu + (3 + i) * fs + (long long)s * 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o[a] = cdf_make(df_half(re[i][a].get()), df_half(im[i][a].get()));
   }
 }
 
@@ -272,26 +315,19 @@ struct MsMom {
   int mom[MS_MAX_MOM][3];
 };
 
-// A operand of the elementals: (D_d v_j)(x)_a at K = 3 x + a from K0
+// A operand of the elementals: (D_d v_j)(x)_a at K = 3 x + a from K0: v_j
+// itself (d = 0) or the stored displaced field d - 1 (nabla_x,y,z, BB_x,y,z)
 struct DispRow {
-  const float2* v;    // v_j [V3][3]                         (d = 0)
-  const CDF* n0;      // N[u][d-1][j] [V3][3]                (d = 1..3)
-  const CDF *nk, *nj; // N[u][k'][j], N[u][j'][j]            (d = 4..6)
-  const float2 *Uj, *Uk;  // links of directions j', k'
-  int d, jd, kd, L, K0;
+  const float2* v;  // v_j [V3][3]            (d = 0)
+  const CDF* f;     // field d - 1 of v_j     (d >= 1)
+  int d, K0;
   __device__ __forceinline__ CDF operator()(int kk) const {
     const int K = K0 + kk;
     if (d == 0) {
       const float2 x = v[K];
       return cdf_make(df_make(x.x, 0.f), df_make(x.y, 0.f));
     }
-    if (d <= 3) return ld_cdf(n0 + K);
-    const int s = K / 3, a = K - 3 * s;
-    // BB = nabla_j'(N_k') - nabla_k'(N_j'), each nabla with its 1/2
-    Dot2 re, im;
-    nabla_acc_df(re, im, 1.f, Uj, nk, site_step(s, L, jd, 1), s, site_step(s, L, jd, -1), a);
-    nabla_acc_df(re, im, -1.f, Uk, nj, site_step(s, L, kd, 1), s, site_step(s, L, kd, -1), a);
-    return cdf_make(df_half(re.get()), df_half(im.get()));
+    return ld_cdf(f + K);
   }
   __device__ __forceinline__ float2 approx(int kk) const {
     const CDF z = (*this)(kk);
@@ -299,9 +335,9 @@ struct DispRow {
   }
 };
 struct DispSrc {  // rows u (7 nv) + d nv + j
-  const float2 *v, *U;
-  const CDF* N;
-  int nv, L, K0;
+  const float2* v;
+  const CDF* N;  // [tb][6][nv][V3][3]
+  int nv, K0;
   long long V3;
   __device__ __forceinline__ DispRow row(long long r) const {
     const long long per = (long long)MS_NDISP * nv;
@@ -310,20 +346,9 @@ struct DispSrc {  // rows u (7 nv) + d nv + j
     const int d = rr / nv, j = rr - d * nv;
     DispRow w{};
     w.d = d;
-    w.L = L;
     w.K0 = K0;
     w.v = v + (u * nv + j) * V3 * 3;
-    const CDF* Nu = N + u * 3 * nv * V3 * 3;
-    if (d >= 1 && d <= 3) w.n0 = Nu + ((long long)(d - 1) * nv + j) * V3 * 3;
-    if (d >= 4) {
-      const int i = d - 4;
-      w.jd = (i + 1) % 3;
-      w.kd = (i + 2) % 3;
-      w.nk = Nu + ((long long)w.kd * nv + j) * V3 * 3;
-      w.nj = Nu + ((long long)w.jd * nv + j) * V3 * 3;
-      w.Uj = U + (u * 3 + w.jd) * V3 * 9;
-      w.Uk = U + (u * 3 + w.kd) * V3 * 9;
-    }
+    if (d >= 1) w.f = N + ((u * 6 + (d - 1)) * nv + j) * V3 * 3;
     return w;
   }
   __device__ __forceinline__ CDF operator()(long long r, int kk) const { return row(r)(kk); }
@@ -405,7 +430,7 @@ __global__ void __launch_bounds__(256) meson_pack_kernel(const CDF* __restrict__
 
 struct MsElemWs {
   CDF* tab;
-  CDF* N;  // nabla fields of the batch [tb][3][nv][V3][3]
+  CDF* N;  // displaced fields of the batch [tb][6][nv][V3][3]: nabla_x,y,z, BB_x,y,z
   void *A, *B;
   int *eA, *eB;
   CDF* acc;  // [tb][7 nv][np nv]
@@ -415,7 +440,7 @@ static MsElemWs carve_melem(Arena& ar, const Scheme& sc, int L, int nv, int np, 
   const long long V3 = (long long)L * L * L, M = (long long)MS_NDISP * nv, R = (long long)np * nv;
   MsElemWs w;
   w.tab = ar.take<CDF>(L);
-  w.N = ar.take<CDF>((size_t)tb * 3 * nv * V3 * 3);
+  w.N = ar.take<CDF>((size_t)tb * 6 * nv * V3 * 3);
   w.A = ar.take<uint16_t>(tc::plane_img_elems(MS_KC, M, tb, 2 * sc.na));
   w.B = ar.take<uint16_t>(tc::plane_img_elems(MS_KC, R, tb, 2 * sc.nb));
   w.eA = ar.take<int>(tb * M);
@@ -427,7 +452,7 @@ static MsElemWs carve_melem(Arena& ar, const Scheme& sc, int L, int nv, int np, 
 // Timeslices per batch: the one K chunk of one timeslice gives
 // ceil(7 N_v / 128) x ceil(N_p N_v / NT) tiles; the batch size with the
 // fullest last wave on the SMs (the largest of those within 2 %) among the
-// batches whose workspace stays within 8 GiB.
+// batches whose workspace stays within 16 GiB.
 static int meson_elem_batch(const Scheme& sc, int L, int nt, int nv, int np) {
   const long long M = (long long)MS_NDISP * nv, R = (long long)np * nv;
   const int NT = R > 64 ? 80 : 32;
@@ -441,7 +466,7 @@ static int meson_elem_batch(const Scheme& sc, int L, int nt, int nv, int np) {
   double eff[4097];
   const int top = nt < 4096 ? nt : 4096;
   for (int tb = 1; tb <= top; ++tb) {
-    if (tb > 1 && one.used + (size_t)(tb - 1) * per > (size_t(8) << 30)) break;
+    if (tb > 1 && one.used + (size_t)(tb - 1) * per > (size_t(16) << 30)) break;
     const long long tiles = tiles1 * tb, waves = (tiles + 147) / 148;
     eff[tb] = (double)tiles / (double)(waves * 148);
     if (eff[tb] > best_eff) best_eff = eff[tb];
@@ -479,6 +504,12 @@ static int melem_batch_run(distil_ctx* ctx, const Scheme& sch, const float2* vt,
     meson_nabla_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(vt, Ut, L, nv, tb, w.N);
   }
   DISTIL_LAUNCH_CHECK();
+  {
+    const long long total = (long long)tb * nv * V3;
+    Launch Lb(ctx, "meson_bb", s);
+    meson_bb_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(Ut, L, nv, tb, w.N);
+  }
+  DISTIL_LAUNCH_CHECK();
   tc::GemmCfg cfg{};
   fill_products(cfg, sch);
   cfg.shift = 2 * H;
@@ -486,7 +517,7 @@ static int melem_batch_run(distil_ctx* ctx, const Scheme& sch, const float2* vt,
   for (long long K0 = 0; K0 < Ktot; K0 += MS_KC) {
     const int Kc = (int)((Ktot - K0) < MS_KC ? (Ktot - K0) : MS_KC);
     const PlaneImg A = tc::plane_img(w.A, Kc, M, tb, NPLA), B = tc::plane_img(w.B, Kc, R, tb, NPLB);
-    DISTIL_TRY((split_rows<false, true, NA>(ctx, "split_meson_disp", DispSrc{vt, Ut, w.N, nv, L, (int)K0, V3},
+    DISTIL_TRY((split_rows<false, true, NA>(ctx, "split_meson_disp", DispSrc{vt, w.N, nv, (int)K0, V3},
                                             tb * M, A, H, w.eA, s)));
     DISTIL_TRY((split_rows<false, true, NB>(ctx, "split_meson_phase", PhConjSrc{vt, w.tab, mom, nv, (int)K0, V3},
                                             tb * R, B, H, w.eB, s)));
@@ -716,7 +747,7 @@ struct QRows {
 //   sum_c sum_alpha i^ph_c(alpha) sum_(i in chunk, j) g_i g_j Phi^(d_c)_ij XT[(b, alpha, i)][(perm_c(alpha), j)]
 // for the N_B profiles of type typ at once.  Block (b, typ, chunk), threads
 // over j.
-constexpr int MS_RED_THREADS = 128;
+constexpr int MS_RED_THREADS = 256;
 __global__ void __launch_bounds__(MS_RED_THREADS) meson_reduce_kernel(const CDF* __restrict__ phiC,
                                                                       const CDF* __restrict__ XT,
                                                                       const DF* __restrict__ g, SpinTab snk, int nv,
@@ -840,10 +871,18 @@ size_t meson_correlate_workspace(int nv, int np, int nb) {
   return ar.used + 256;
 }
 
+// 80-wide tiles on the persistent kernel with one accumulator set (the MMAs
+// of a tile wait for the previous tile's epilogue while the copies of the
+// next run; K = 4 N_v is short, so the epilogue of one tile per CTA would
+// otherwise sit between the copies); 32-wide one-tile launches for N <= 64.
 template <int NT>
 static int mcorr_gemm(distil_ctx* ctx, const char* name, const PlaneImg& A, const PlaneImg& B,
                       const tc::GemmCfg& cfg, const EpiStoreCDF& epi, cudaStream_t s) {
-  return tc::launch_gemm<NT, 16, 6, 8, tc::max_stages<NT, 16, 6, 8>(), false, 3>(ctx, name, A, B, cfg, 1, epi, s);
+  if constexpr (NT == 80)
+    return tc::launch_gemm_persistent<80, 16, 6, 8, tc::max_stages<80, 16, 6, 8>(), false, 3, 1>(ctx, name, A, B,
+                                                                                               cfg, 1, epi, s);
+  else
+    return tc::launch_gemm<NT, 16, 6, 8, tc::max_stages<NT, 16, 6, 8>(), false, 3>(ctx, name, A, B, cfg, 1, epi, s);
 }
 
 int meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, const void* tau, int nt, int nv,
@@ -936,52 +975,84 @@ int meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, c
 
 // --------------------------------------------------------------- pruning
 
-// One-sided (Hestenes) Jacobi SVD of A = C(t_p) (nops <= 32, one warp, lane
-// = row): column pairs are rotated until orthogonal, A V = W; the singular
+// One-sided (Hestenes) Jacobi SVD of A = C(t_p) (nops <= 32 columns, lane =
+// row): column pairs are rotated until orthogonal, A V = W; the singular
 // values are the column norms of W and the left singular vectors its
-// normalised columns.  Output: the n columns of the largest singular values,
-// each scaled so that its largest-modulus component (the first of equal
-// ones) is real and positive, and all singular values, descending.
-__global__ void __launch_bounds__(32) meson_svd_kernel(const double2* __restrict__ C, int nops, int nt, int tp,
-                                                       int nkeep, double2* __restrict__ Un, double* __restrict__ sv) {
+// normalised columns.  The pairs of a sweep run in the round-robin
+// (circle) order, the n/2 disjoint pairs of a round on n/2 warps at once.
+// Output: the n columns of the largest singular values, each scaled so that
+// its largest-modulus component (the first of equal ones) is real and
+// positive, and all singular values, descending.
+constexpr int MS_SVD_WARPS = 16;
+__global__ void __launch_bounds__(32 * MS_SVD_WARPS) meson_svd_kernel(const double2* __restrict__ C, int nops, int nt,
+                                                                      int tp, int nkeep, double2* __restrict__ Un,
+                                                                      double* __restrict__ sv) {
   __shared__ double2 A[32][33];
-  __shared__ double nrm[32];
+  __shared__ double nrm[32], offw[MS_SVD_WARPS];
   __shared__ int order[32];
-  const int q = blockIdx.x, lane = threadIdx.x;
+  __shared__ int done;
+  const int q = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double2* Cq = C + (long long)q * nops * nops * nt;
-  for (int c = 0; c < nops; ++c)
-    A[lane][c] = lane < nops ? Cq[((long long)lane * nops + c) * nt + tp] : make_double2(0.0, 0.0);
-  __syncwarp();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    int rotated = 0;
-    for (int p = 0; p < nops - 1; ++p)
-      for (int r = p + 1; r < nops; ++r) {
-        const double2 ap = A[lane][p], ar = A[lane][r];
-        double al = ap.x * ap.x + ap.y * ap.y, be = ar.x * ar.x + ar.y * ar.y;
-        double gr = ap.x * ar.x + ap.y * ar.y, gi = ap.x * ar.y - ap.y * ar.x;  // conj(ap) ar
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          gr += __shfl_xor_sync(0xffffffffu, gr, o);
-          gi += __shfl_xor_sync(0xffffffffu, gi, o);
-        }
-        const double ga = sqrt(gr * gr + gi * gi);
-        if (!(ga > 1e-14 * sqrt(al * be))) continue;
-        ++rotated;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        const double er = gr / ga, ei = gi / ga;  // e^{i phi}
-        // a_p' = c a_p - s e^{-i phi} a_r,  a_r' = s e^{i phi} a_p + c a_r
-        const double2 np_ = make_double2(c * ap.x - s * (er * ar.x + ei * ar.y), c * ap.y - s * (er * ar.y - ei * ar.x));
-        const double2 nr_ = make_double2(s * (er * ap.x - ei * ap.y) + c * ar.x, s * (er * ap.y + ei * ap.x) + c * ar.y);
-        A[lane][p] = np_;
-        A[lane][r] = nr_;
-        __syncwarp();
-      }
-    if (!rotated) break;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    A[r][c] = (r < nops && c < nops) ? Cq[((long long)r * nops + c) * nt + tp] : make_double2(0.0, 0.0);
   }
-  __syncwarp();
+  const int n = (nops + 1) & ~1;  // even number of columns for the circle order
+  if (threadIdx.x == 0) done = 0;
+  __syncthreads();
+  for (int sweep = 0; sweep < 40 && !done; ++sweep) {
+    double off = 0.0;  // largest |a_p^H a_r| / (|a_p| |a_r|) this warp met
+    for (int round = 0; round < n - 1; ++round) {
+      if (w < n / 2) {
+        int p, r;
+        if (w == 0) {
+          p = round;
+          r = n - 1;
+        } else {
+          p = (round + w) % (n - 1);
+          r = (round - w + n - 1) % (n - 1);
+        }
+        if (p > r) {
+          const int x = p;
+          p = r;
+          r = x;
+        }
+        if (r < nops) {
+          const double2 ap = A[lane][p], ar = A[lane][r];
+          double al = ap.x * ap.x + ap.y * ap.y, be = ar.x * ar.x + ar.y * ar.y;
+          double gr = ap.x * ar.x + ap.y * ar.y, gi = ap.x * ar.y - ap.y * ar.x;  // conj(ap) ar
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gi += __shfl_xor_sync(0xffffffffu, gi, o);
+          }
+          const double ga = sqrt(gr * gr + gi * gi);
+          const double nab = sqrt(al * be);
+          if (nab > 0.0) off = fmax(off, ga / nab);
+          if (ga > 1e-15 * nab) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+            const double er = gr / ga, ei = gi / ga;  // e^{i phi}
+            // a_p' = c a_p - s e^{-i phi} a_r,  a_r' = s e^{i phi} a_p + c a_r
+            A[lane][p] = make_double2(c * ap.x - s * (er * ar.x + ei * ar.y), c * ap.y - s * (er * ar.y - ei * ar.x));
+            A[lane][r] = make_double2(s * (er * ap.x - ei * ap.y) + c * ar.x, s * (er * ap.y + ei * ap.x) + c * ar.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (lane == 0) offw[w] = off;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int k = 0; k < MS_SVD_WARPS; ++k) m = fmax(m, offw[k]);
+      done = m < 1e-13;  // columns orthogonal to well below the FP64 rounding of the data
+    }
+    __syncthreads();
+  }
+  if (w != 0) return;
   if (lane < nops) {
     double s2 = 0.0;
     for (int r = 0; r < nops; ++r) s2 += A[r][lane].x * A[r][lane].x + A[r][lane].y * A[r][lane].y;
@@ -1002,8 +1073,8 @@ __global__ void __launch_bounds__(32) meson_svd_kernel(const double2* __restrict
   if (lane < nops && sv) sv[(long long)q * nops + lane] = nrm[order[lane]];
   for (int m = 0; m < nkeep; ++m) {
     const int c = order[m];
-    const double n = nrm[c];
-    double2 u = lane < nops && n > 0.0 ? make_double2(A[lane][c].x / n, A[lane][c].y / n) : make_double2(0.0, 0.0);
+    const double nm = nrm[c];
+    double2 u = lane < nops && nm > 0.0 ? make_double2(A[lane][c].x / nm, A[lane][c].y / nm) : make_double2(0.0, 0.0);
     // phase: the largest-modulus component (first of equal ones) real positive
     double best = lane < nops ? u.x * u.x + u.y * u.y : -1.0;
     int arg = lane;
@@ -1063,7 +1134,7 @@ int meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt, int tp
                 double* sv, cudaStream_t s) {
   {
     Launch L(ctx, "meson_prune", s);
-    meson_svd_kernel<<<np, 32, 0, s>>>((const double2*)C, nops, nt, tp, nkeep, (double2*)Un, sv);
+    meson_svd_kernel<<<np, 32 * MS_SVD_WARPS, 0, s>>>((const double2*)C, nops, nt, tp, nkeep, (double2*)Un, sv);
     meson_project_kernel<<<dim3(np, nt), 256, 0, s>>>((const double2*)C, (const double2*)Un, nops, nt, nkeep,
                                                       (double2*)Ct);
   }

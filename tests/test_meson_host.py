@@ -21,8 +21,8 @@ def _ws(fn, *args):
 def test_meson_workspace_queries(L):
     st, b = _ws(L.distil_meson_elementals_workspace, 24, 48, 200, 1, distil.MODES["fp16x6"])
     assert st == 0 and b > 0
-    # the batch of timeslices keeps the elementals workspace within 8 GiB plus one timeslice
-    assert b < (9 << 30)
+    # the batch of timeslices keeps the elementals workspace within 16 GiB plus one timeslice
+    assert b < (17 << 30)
     st1, b1 = _ws(L.distil_meson_elementals_workspace, 24, 1, 200, 1, distil.MODES["fp16x6"])
     assert st1 == 0 and 0 < b1 <= b
     st, c = _ws(L.distil_meson_correlate_workspace, 200, 1, 7, distil.MODES["fp16x6"])
