@@ -1181,6 +1181,14 @@ def meson_bytes(name, m):
     return table.get(name)
 
 
+# DRAM bytes (read + write) per launch of the meson elementals GEMM, from one
+# ncu capture of the L=24, N_v=200 workload cut to 4 timeslices (one 4032-long
+# K chunk of 4 timeslices: 443.8 MB read, 3.9 MB written, the operand planes of
+# the chunk and the accumulator) scaled by the timeslices of a bench launch
+# (16 per batch): x 4.
+MESON_TRAFFIC = {("L24_Nt48_Nv200_meson", "tc_gemm_meson_elem"): (443.8e6 + 3.9e6) * 16 / 4}
+
+
 def meson_rooflines(kstats, m, pk, steps):
     tpeak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1400.0
     hpeak = pk.get("hbm_gbs") or 6400.0
@@ -1356,7 +1364,7 @@ def run_meson(args):
             "gpu_launches": int(sum(l for l, _ in kstats.values())),
             "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in sorted(kstats.items(),
                                                                                   key=lambda kv: -kv[1][1])},
-            "roofline": None if dom is None else {**dom, "traffic": None},
+            "roofline": None if dom is None else {**dom, "traffic": MESON_TRAFFIC.get((m.name, dom["kernel"]))},
             "kernel_rooflines": roofs,
             "whole_step": {"issued_tflops": issued / (ms_step / 1e3) / 1e12,
                            "frac": issued / (ms_step / 1e3) / 1e12 / tpeak, "peak": tpeak,
