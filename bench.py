@@ -14,6 +14,7 @@ plain FP32/FP64 CUDA-core paths are reported beside it.
 
 --meson charm times the one-meson path instead (L=24, N_t=48, N_v=200,
 3 Gammas x 7 profiles, pruned to 8 x 8): one step = one configuration.
+--glueball charm times the A1-+ glueball operators on the same links.
 
 Default: workload 5 (L=48, N_t=96, N_v=256, 9 momenta, 8 profiles), mode
 fp16x6, one step = one sink timeslice of it (elementals of every momentum,
@@ -1381,6 +1382,117 @@ def run_meson(args):
     return out
 
 
+# --------------------------------------------------------------------------- glueballs
+
+GLUE_METRIC = "glueball O_n(t) values/s"
+FP64_NOMINAL_GFLOPS = 1250.0   # B300 FP64, nominal (no measured FP64 peak in the peaks file)
+
+
+def glue_flops(name, L, nt):
+    """FP64 flops (8 per complex multiply-add of 3 x 3 products) one
+    configuration asks of each glueball kernel family, per site: clover
+    3 planes x 4 plaquettes x 3 products x 27; 39 derivative fields x 4
+    products x 27; traces 4 x 6 x 9 + 6 x 27 + 12 x 9."""
+    V3 = L ** 3
+    table = {
+        "glue_clover": (8.0 * 3 * 4 * 3 * 27 * V3 * nt, "3 planes x 4 plaquettes x 3 products per site"),
+        "glue_deriv": (8.0 * 39 * 4 * 27 * V3 * nt, "39 adjoint derivatives x 4 products per site"),
+        "glue_trace": (8.0 * (4 * 6 * 9 + 6 * 27 + 12 * 9) * V3 * nt, "the five traces per site"),
+    }
+    return table.get(name)
+
+
+def run_glueball(args):
+    """One step = the five A1-+ glueball operators of every timeslice of one
+    configuration (links of the meson workload: L = 24, N_t = 48)."""
+    m = synth.meson_config(args.glueball, 0)
+    log(f"generating links of {m.name}")
+    U_h = m.all_links().astype(np.complex64)
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    from paper_2609_37723_b300 import distil
+    U_pin = torch.from_numpy(np.ascontiguousarray(U_h)).pin_memory()
+    U = U_pin.to(dev)
+    O = torch.empty((m.nt, 5), dtype=torch.complex128, device=dev)
+    ws = torch.empty(distil.glueball_workspace(m.L, m.nt), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(UU):
+        distil.glueball_operators(UU, m.L, out=O, workspace=ws)
+
+    for _ in range(args.warmup):
+        step(U)
+    torch.cuda.synchronize()
+    distil.profile_enable(timing=True, device=0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        step(U)
+    torch.cuda.nvtx.range_pop()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kstats = distil.profile_read(device=0)
+    distil.profile_enable(timing=False, device=0)
+    ms_step = ms / args.steps
+    values = 5 * m.nt
+    U_in = torch.empty_like(U)
+    O_host = torch.empty(O.shape, dtype=O.dtype).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        U_in.copy_(U_pin, non_blocking=True)
+        step(U_in)
+        O_host.copy_(O, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = values * e2e_steps / (e0.elapsed_time(e1) / 1e3)
+    roofs = []
+    for name, (launches, kms) in sorted(kstats.items(), key=lambda kv: -kv[1][1]):
+        f = glue_flops(name, m.L, m.nt)
+        if f is None or kms <= 0:
+            continue
+        ach = f[0] * args.steps / (kms / 1e3) / 1e9
+        roofs.append({"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS,
+                      "unit": "GFLOP/s (FP64)", "frac": ach / FP64_NOMINAL_GFLOPS, "ms_per_step": kms / args.steps,
+                      "launches": launches, "per_unit": f[1], "peak_kind": "of nominal"})
+    dom = max(roofs, key=lambda r: r["ms_per_step"]) if roofs else None
+    cpu, parity = None, None
+    if not args.no_cpu_baseline:
+        from oracle import glueball as og
+        t0 = time.perf_counter()
+        ref = og.operators_t(U_h[1].astype(np.complex128), m.L)
+        sec = time.perf_counter() - t0
+        cpu = {"value": 5 / sec, "unit": GLUE_METRIC, "cores": OracleSlices.cores(), "kind": "oracle",
+               "sample": f"one timeslice (t = 1) of {m.nt}: {sec:.1f} s, numpy FP64", "seconds": sec}
+        got = O[1].cpu().numpy()
+        parity = {"reference": "FP64 oracle, timeslice t = 1",
+                  "max_err_rel_to_largest": float(np.abs(got - ref).max() / np.abs(ref).max())}
+    return {
+        "metric": GLUE_METRIC, "value": values / (ms_step / 1e3), "unit": "values/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Haar SU(3) links of the meson workload)",
+        "config": {"workload": m.name.replace("meson", "glueball"), "L": m.L, "nt": m.nt,
+                   "step": "one configuration: B_i, 39 adjoint derivative fields and O_1..O_5 of every timeslice",
+                   "parallelism": "single GPU", "l2": "derivative fields (113 MB per timeslice) larger than L2"},
+        "e2e": {"value": e2e, "unit": "values/s", "h2d_bytes_per_step": int(U_pin.numel() * 8),
+                "d2h_bytes_per_step": int(O_host.numel() * 16)},
+        "gpu_launches": int(sum(l for l, _ in kstats.values())),
+        "kernels": {k: {"launches": l, "ms": round(t, 3)} for k, (l, t) in kstats.items()},
+        "roofline": None if dom is None else {**dom, "traffic": None},
+        "kernel_rooflines": roofs,
+        "clocks": clk, "parity": parity, "cpu_baseline": cpu,
+    }
+
+
 def spawn_ranks(n: int) -> int:
     """bench.py --gpus N run without a launcher: start N ranks of this script
     under torch.distributed.run on this node (127.0.0.1) and return its exit
@@ -1415,6 +1527,8 @@ def main():
                     help="keep only the first NT timeslices (profiling a smaller case; not a bench number)")
     ap.add_argument("--meson", default=None, choices=["charm", "small"],
                     help="time the one-meson path on this workload instead (charm: L=24, N_t=48, N_v=200)")
+    ap.add_argument("--glueball", default=None, choices=["charm", "small", "tiny"],
+                    help="time the A1-+ glueball operators on the links of this meson workload")
     ap.add_argument("--np", type=int, default=0,
                     help="workloads 1-3: keep only the first NP momenta (profiling a smaller case; not a bench number)")
     args = ap.parse_args()
@@ -1422,7 +1536,9 @@ def main():
         sys.exit(spawn_ranks(args.gpus))
     if args.warmup < 3 and args.impl == "ours" and (args.workload == 5 or args.meson):
         ap.error("--warmup must be >= 3")
-    if args.meson and args.impl == "ours":
+    if args.glueball and args.impl == "ours":
+        out = run_glueball(args)
+    elif args.meson and args.impl == "ours":
         out = run_meson(args)
     elif args.impl == "reference":
         out = run_reference(args)

@@ -464,6 +464,33 @@ int distil_meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi
 int distil_meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt, int t_prune, int nkeep,
                        void* Ct, void* Un, double* sv, distil_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* A1^{-+} glueball operators                                          */
+/* ------------------------------------------------------------------ */
+/* Paper Sec. 2.2 ("Improved glueball operators"): operators built from the
+ * chromo-magnetic field B_i = eps_ijk F_jk (clover discretisation of the
+ * field strength) and adjoint gauge-covariant symmetric differences D_j. */
+
+int distil_glueball_workspace(int L, int nt, size_t* bytes);
+
+/* O[t][n], n = 0..4, the five A1^{-+} operators of timeslice t at zero
+ * momentum (repeated indices summed, eps the Levi-Civita symbol):
+ *   O_1 = sum_x Tr(eps_ijk B_i D_j B_k)
+ *   O_2 = sum_x Tr(eps_ijk eps_ilm B_j B_k D_l B_m)
+ *   O_3 = sum_x Tr(eps_ijk B_i D_j^3 B_k)
+ *   O_4 = sum_x Tr(eps_ijk B_i D_j^2 D_k B_j)
+ *   O_5 = sum_x Tr(eps_ijk B_i D_j D_i^2 B_k)
+ * with F_{mu nu}(x) = (Q - Q^dagger) / (8 i) minus a third of its trace, Q
+ * the sum of the four counter-clockwise plaquettes of the (mu, nu) plane
+ * that start and end at x; B_i = 2 F_jk for (i, j, k) cyclic; (D_j X)(x) =
+ * 1/2 [U_j(x) X(x+j) U_j(x)^dagger - U_j(x-j)^dagger X(x-j) U_j(x-j)],
+ * D_j^2 = D_j D_j (lattice units, periodic space).
+ *   U  [nt][3][L^3][3][3]  c64 device: U[t][k][s][a][b], as for the mesons
+ *   O  [nt][5]             c128 device, fully overwritten
+ * FP64 on CUDA cores (deterministic sums).  Sizes: 2 <= L <= 128, nt >= 1. */
+int distil_glueball_operators(distil_ctx* ctx, const void* U, int L, int nt, void* O, void* workspace,
+                              size_t ws_bytes, distil_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,10 @@ int meson_correlate(distil_ctx* ctx, const void* phi_snk, const void* phi_src, c
 int meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt, int tp, int nkeep, void* Ct, void* Un,
                 double* sv, cudaStream_t s);
 
+size_t glueball_workspace(int L, int nt);
+int glueball_operators(distil_ctx* ctx, const void* U, int L, int nt, void* O, void* ws, size_t ws_bytes,
+                       cudaStream_t s);
+
 Profiler& profiler(distil_ctx* ctx) { return *ctx->prof; }
 
 // Lowest index of a NaN or Inf among x[0, count) into the 64-bit word *slot
@@ -394,6 +398,34 @@ int distil_meson_prune(distil_ctx* ctx, const void* C, int np, int nops, int nt,
   DISTIL_CHECK_ARG(aligned(C, 16) && aligned(Ct, 16) && aligned(Un, 16) && aligned(sv, 8),
                    "distil_meson_prune: misaligned pointer");
   return meson_prune(ctx, C, np, nops, nt, t_prune, nkeep, Ct, Un, sv, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------- glueball path
+
+int distil_glueball_workspace(int L, int nt, size_t* bytes) {
+  g_err[0] = 0;
+  DISTIL_CHECK_ARG(bytes != nullptr, "bytes is null");
+  DISTIL_CHECK_ARG(L >= 2 && L <= MS_LIMIT_L && nt >= 1, "distil_glueball_workspace: 2 <= L <= %d, nt >= 1",
+                   MS_LIMIT_L);
+  *bytes = glueball_workspace(L, nt);
+  return DISTIL_OK;
+}
+
+int distil_glueball_operators(distil_ctx* ctx, const void* U, int L, int nt, void* O, void* workspace,
+                              size_t ws_bytes, distil_stream stream) {
+  g_err[0] = 0;
+  DISTIL_TRY(enter(ctx));
+  DISTIL_CHECK_ARG(L >= 2 && L <= MS_LIMIT_L && nt >= 1, "distil_glueball_operators: 2 <= L <= %d, nt >= 1",
+                   MS_LIMIT_L);
+  DISTIL_CHECK_ARG(U && O && workspace, "distil_glueball_operators: null pointer");
+  DISTIL_CHECK_ARG(aligned(U, 8) && aligned(O, 16) && aligned(workspace, 256),
+                   "distil_glueball_operators: misaligned pointer (arrays to their element, workspace to 256 bytes)");
+  const size_t need = glueball_workspace(L, nt);
+  if (ws_bytes < need) {
+    set_error("distil_glueball_operators: workspace %zu < %zu bytes", ws_bytes, need);
+    return DISTIL_ENOMEM;
+  }
+  return glueball_operators(ctx, U, L, nt, O, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int distil_mode_supported(int mode) {

@@ -40,7 +40,8 @@ EXPORTS = ["distil_create", "distil_destroy", "distil_last_error",
            "distil_plan_workspace", "distil_plan_create", "distil_plan_run", "distil_plan_info",
            "distil_plan_destroy", "distil_set_wait_limit", "distil_scan_finite",
            "distil_profiles_eigen", "distil_meson_elementals_workspace", "distil_meson_elementals",
-           "distil_meson_correlate_workspace", "distil_meson_correlate", "distil_meson_prune"]
+           "distil_meson_correlate_workspace", "distil_meson_correlate", "distil_meson_prune",
+           "distil_glueball_workspace", "distil_glueball_operators"]
 
 _lib = None
 _ctx = {}
@@ -147,6 +148,11 @@ def _declare(L):
     L.distil_meson_prune.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                      c_void_p, c_void_p]
     L.distil_meson_prune.restype = c_int
+    L.distil_glueball_workspace.argtypes = [c_int, c_int, P(c_size_t)]
+    L.distil_glueball_workspace.restype = c_int
+    L.distil_glueball_operators.argtypes = [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_size_t,
+                                            c_void_p]
+    L.distil_glueball_operators.restype = c_int
     L.distil_profile_read.argtypes = [c_void_p, P(KernelStat), c_int, P(c_int)]
     L.distil_profile_read.restype = c_int
 
@@ -608,3 +614,27 @@ def meson_prune(C, t_prune: int, nkeep: int, stream=None):
     _check(lib().distil_meson_prune(context(C.device.index or 0), _ptr(C), np_, nops, nt, int(t_prune), int(nkeep),
                                     _ptr(Ct), _ptr(Un), _ptr(sv), _stream(stream)))
     return Ct, Un, sv
+
+
+# ---------------------------------------------------------------- glueballs
+
+
+def glueball_workspace(L: int, nt: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().distil_glueball_workspace(L, nt, ctypes.byref(b)))
+    return b.value
+
+
+def glueball_operators(U, L: int, out=None, workspace=None, stream=None):
+    """U [nt][3][L^3][3][3] c64 (GPU) -> O [nt][5] c128, the five A1-+
+    glueball operators of every timeslice."""
+    import torch
+    nt = int(U.shape[0])
+    assert U.is_cuda and U.is_contiguous() and U.dtype == torch.complex64 and tuple(U.shape[1:]) == (3, L ** 3, 3, 3)
+    if out is None:
+        out = torch.empty((nt, 5), dtype=torch.complex128, device=U.device)
+    if workspace is None:
+        workspace = _workspace(glueball_workspace(L, nt), U.device)
+    _check(lib().distil_glueball_operators(context(U.device.index or 0), _ptr(U), L, nt, _ptr(out), _ptr(workspace),
+                                           _nbytes(workspace), _stream(stream)))
+    return out

@@ -56,3 +56,13 @@ def test_meson_calls_without_context_fail_cleanly(L):
     assert L.distil_meson_prune(None, None, 1, 21, 4, 0, 8, None, None, None, None) == 1
     assert L.distil_meson_correlate(None, None, None, None, 4, 16, 1, None, 7, distil.MODES["fp16x6"], None, None,
                                     0, None) == 1
+
+
+def test_glueball_workspace_and_sizes(L):
+    b = ctypes.c_size_t()
+    assert L.distil_glueball_workspace(24, 48, ctypes.byref(b)) == 0
+    # 57 complex128 3 x 3 fields per site and timeslice, batched within 4 GiB
+    assert 57 * 24 ** 3 * 144 < b.value < (5 << 30)
+    for bad in [(1, 4), (129, 4), (8, 0)]:
+        assert L.distil_glueball_workspace(*bad, ctypes.byref(b)) == 1
+    assert L.distil_glueball_operators(None, None, 8, 4, None, None, 0, None) == 1

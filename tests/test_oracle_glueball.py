@@ -153,3 +153,19 @@ def test_operators_brute_force_o1():
             DB = 0.5 * (U[j, s] @ B[k, sp] @ d(U[j, s]) - d(U[j, sm]) @ B[k, sm] @ U[j, sm])
             total += e * np.trace(B[i, s] @ DB)
     assert abs(og.operators_t(U, L)[0] - total) < 1e-10 * (1 + abs(total))
+
+
+def test_summation_by_parts_relates_o4_and_o5():
+    """D_j is anti-self-adjoint under sum_x Tr (periodic boundaries:
+    sum_x Tr(X D_j Y) = -sum_x Tr((D_j X) Y)), and two summations by parts
+    and a relabelling turn O_5 as printed into -O_4: the identity holds on
+    the lattice to rounding."""
+    L = 4
+    U = _links(L, 10)
+    O = og.operators_t(U, L)
+    assert abs(O[3] + O[4]) < 1e-10 * abs(O[3])
+    B = og.magnetic(U, L)
+    X, Y = B[0], og.adj_deriv(U, B[1], L, 2)
+    lhs = np.einsum("sab,sba->", X, og.adj_deriv(U, Y, L, 1))
+    rhs = -np.einsum("sab,sba->", og.adj_deriv(U, X, L, 1), Y)
+    assert abs(lhs - rhs) < 1e-10 * (1 + abs(lhs))
