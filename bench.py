@@ -1406,6 +1406,8 @@ def run_glueball(args):
     """One step = the five A1-+ glueball operators of every timeslice of one
     configuration (links of the meson workload: L = 24, N_t = 48)."""
     m = synth.meson_config(args.glueball, 0)
+    if args.nt > 0:
+        m.base = dataclasses.replace(m.base, nt=min(args.nt, m.nt))
     log(f"generating links of {m.name}")
     U_h = m.all_links().astype(np.complex64)
     import torch
