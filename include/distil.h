@@ -61,7 +61,7 @@ typedef enum {
   DISTIL_ENOMEM = 2,   /* workspace too small / allocation failed          */
   DISTIL_ECUDA = 3,    /* a CUDA runtime or driver call failed             */
   DISTIL_ETIMEOUT = 4, /* a bounded device-side wait expired               */
-  DISTIL_ENOTSUP = 5   /* mode or size not supported by this build         */
+  DISTIL_ENOTSUP = 5   /* mode or size not supported by the library       */
 } distil_status;
 
 /* Arithmetic of a call.
@@ -375,7 +375,7 @@ int distil_set_wait_limit(distil_ctx* ctx, long long cycles);
 int distil_scan_finite(distil_ctx* ctx, const void* x, long long count, int is_f32,
                        long long* first_bad, distil_stream stream);
 
-/* 1 if this build implements `mode`, else 0 (no device needed). */
+/* 1 if the library implements `mode`, else 0 (no device needed). */
 int distil_mode_supported(int mode);
 
 /* Per-kernel statistics of the library's own launches. */
