@@ -1177,6 +1177,8 @@ def meson_bytes(name, m):
     table = {
         "meson_nabla": ((8.0 * n * 3 * V3 + 3 * 72.0 * V3 + 3 * 16.0 * n * 3 * V3) * nt,
                         "v (8 B) and the links read, three nabla fields (16 B) written, per t"),
+        "meson_bb": (2 * 3 * 16.0 * n * 3 * V3 * nt,
+                     "three nabla fields read, three BB fields written (16 B per value) per t"),
         "meson_reduce": (16.0 * nops * 16 * n * n * m.np_ * nt, "X (3 N_B (4 N_v)^2 x 16 B) read per (t, p)"),
     }
     return table.get(name)

@@ -73,3 +73,35 @@ def test_elementals_issued_tiles_count_the_triangle_skip():
     dense = -(-P2 // 128) * 128 * -(-R // 128) * 128 * 3 * q.V3
     assert 3 * q.V3 * q.T3 * q.np_ < issued < dense
     assert K == 192
+
+
+def test_meson_rooflines_follow_the_per_unit_work():
+    import bench
+    from paper_2609_37723_b300 import synth
+    m = synth.meson_config("charm")
+    n, V3, nops = m.nv, m.V3, 3 * m.nb
+    ks = {"tc_gemm_meson_elem": (33, 1000.0), "tc_gemm_meson_q": (48, 1000.0), "meson_bb": (3, 1000.0),
+          "meson_pack": (3, 1000.0)}
+    pk = {"bf16_tflops_sustained": 1000.0, "hbm_gbs": 5000.0}
+    rows = {r["kernel"]: r for r in bench.meson_rooflines(ks, m, pk, 1)}
+    assert set(rows) == {"tc_gemm_meson_elem", "tc_gemm_meson_q", "meson_bb"}
+    # elementals: 7 displacements x N_p N_v^2 x 3 V3 complex MACs per timeslice, 8 split products
+    assert rows["tc_gemm_meson_elem"]["achieved"] == pytest.approx(8 * 8 * 7.0 * n * m.np_ * n * 3 * V3 * m.nt / 1e12)
+    # GEMM 1: 3 N_B (4 N_v)^3 per (t, p), 6 split products
+    assert rows["tc_gemm_meson_q"]["achieved"] == pytest.approx(8 * 6 * nops * 64.0 * n ** 3 * m.np_ * m.nt / 1e12)
+    assert rows["meson_bb"]["bound"] == "hbm"
+    assert rows["meson_bb"]["achieved"] == pytest.approx(96.0 * n * 3 * V3 * m.nt / 1e9)
+    # the elementals traffic entry scales a 4-timeslice capture to a 16-timeslice launch
+    assert bench.MESON_TRAFFIC[(m.name, "tc_gemm_meson_elem")] == pytest.approx(447.7e6 * 4)
+
+
+def test_glueball_flop_model():
+    import bench
+    L, nt = 24, 48
+    V3 = L ** 3
+    clover = bench.glue_flops("glue_clover", L, nt)[0]
+    deriv = bench.glue_flops("glue_deriv", L, nt)[0]
+    trace = bench.glue_flops("glue_trace", L, nt)[0]
+    # 45360 FP64 flops per site and timeslice in all: 8 x (972 + 4212 + 486) complex multiply-adds
+    assert (clover + deriv + trace) / (V3 * nt) == pytest.approx(8 * (972 + 4212 + 486))
+    assert bench.glue_flops("glue_final", L, nt) is None
