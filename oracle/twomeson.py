@@ -29,6 +29,7 @@ momentum and back-to-back momenta; no GEVP is solved with it):
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg
 
 from . import meson
 
@@ -43,7 +44,6 @@ def optimal_weights(C: np.ndarray, t_prune: int, nkeep: int, t0: int, td: int, s
     Ct, Un, _ = meson.prune(C, t_prune, nkeep)
     out = np.empty((C.shape[0], C.shape[1]), dtype=np.complex128)
     for p in range(C.shape[0]):
-        import scipy.linalg
         lam, vecs = scipy.linalg.eig(Ct[p, :, :, td], Ct[p, :, :, t0])
         order = np.argsort(-np.abs(lam), kind="stable")
         u = vecs[:, order[state]]

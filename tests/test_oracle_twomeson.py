@@ -10,12 +10,9 @@ rank-n matrix whose optimal operators are known."""
 import itertools
 
 import numpy as np
-import pytest
 
 from oracle import meson as om
 from oracle import twomeson as tm
-
-LETTERS = "abcdefghijklmnop"
 
 
 def _perm_sign(p):
